@@ -1,0 +1,173 @@
+/*
+ * swcorr.h -- C ABI of the GB300 sliding-window inter-channel correlation
+ * library (libswcorr.so).
+ *
+ * The library computes, for two equal-size grids x and y (Poyda & Zhizhin,
+ * arXiv:1807.06507, Section 3: "both sets of data must be the same size"),
+ * the Pearson correlation of every sliding window (Introduction, Eq. 1)
+ * through the sums form (Section 1, Eq. 2):
+ *
+ *     c = (n Sxy - Sx Sy) / ( sqrt(n Sxx - Sx^2) * sqrt(n Syy - Sy^2) )
+ *
+ * with the five window sums Sx, Sy, Sxx, Syy, Sxy obtained by separable
+ * sliding summation, one pass per dimension (Section 1, steps 1-4 and the
+ * n-dimensional generalisation).  The result for a window is written to the
+ * window's middle cell (Section 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Dimensions are listed outermost first (C order): for a 2-D grid
+ *   shape = {rows, cols}, for 3-D {planes, rows, cols}; the last dimension
+ *   is contiguous in memory.
+ * - Window: k[d] cells along dimension d, centred: output centre i covers
+ *   [i - floor((k-1)/2), i + floor(k/2)].  Border rule SWCORR_BORDER_CLIP:
+ *   the window is clipped to the grid and n is the number of in-bounds cells
+ *   (the paper writes -2 at borders instead; that mode is not provided).
+ * - Stride ("step of the window", Introduction): output j has centre
+ *   j * stride[d]; the output has ceil(shape[d] / stride[d]) cells per
+ *   dimension.
+ * - A window whose x (or y) values are all equal has zero variance and
+ *   yields NaN.  This is the paper's equality check (Section 3, accuracy
+ *   discussion), decided exactly.
+ * - Results are float32 and clamped to [-1, 1].
+ * - Pitches are in ELEMENTS per dimension (in_pitch[d] = distance between
+ *   consecutive indices of dimension d); pitch[ndim-1] must be 1.  NULL means
+ *   contiguous.
+ *
+ * Numerics
+ * --------
+ * - SWCORR_U16: the five sums are exact integers; c is evaluated from them
+ *   with float32 rounding only in the last steps (|error| < 1e-6).
+ * - SWCORR_F32: each input value is first offset by a per-block reference
+ *   and rounded to a fixed-point grid of 2^-22 times the block's value range;
+ *   from there on the sums are exact integers.  Integer-valued data whose
+ *   block range is below 2^22 is represented exactly.
+ *
+ * Memory ownership and errors
+ * ---------------------------
+ * The caller owns every data buffer and keeps it alive until the work queued
+ * on the given stream has completed.  The library owns plans (tensor-map
+ * cache, a small device status block, staging buffers for host runs).
+ * No call throws; each returns a status and records a detail message that
+ * swcorr_last_error() returns (per thread).  Launch errors are reported
+ * synchronously by the run call; device-side errors (a bounded wait that ran
+ * out) are latched in the plan's status block and reported by
+ * swcorr_plan_status() after the stream has been synchronised.
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ * default stream).
+ */
+#ifndef SWCORR_H
+#define SWCORR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SWCORR_OK = 0,
+  SWCORR_ERR_INVALID_ARG = 1, /* a shape, window, stride, pointer or pitch is invalid */
+  SWCORR_ERR_UNSUPPORTED = 2, /* valid but not provided (e.g. ndim > 3, kw > 31) */
+  SWCORR_ERR_ALIGNMENT = 3,   /* base address or pitch not 16-byte aligned */
+  SWCORR_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed */
+  SWCORR_ERR_OOM = 5,         /* the library could not allocate what it needs */
+  SWCORR_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (kernel returned early) */
+  SWCORR_ERR_NO_DEVICE = 7    /* no usable sm_103 device */
+} swcorr_status;
+
+typedef enum { SWCORR_U16 = 1, SWCORR_F32 = 2 } swcorr_dtype;
+
+typedef enum { SWCORR_BORDER_CLIP = 0 } swcorr_border;
+
+enum {
+  /* Also write the five window sums (int64: Sx, Sy, Sxx, Syy, Sxy per output,
+   * output-major) to the sums buffer passed to swcorr_run.  uint16 only; the
+   * sums are the exact integer sums of Section 1, steps 1-3. */
+  SWCORR_FLAG_EMIT_SUMS = 1u
+};
+
+typedef struct swcorr_plan_s* swcorr_plan;
+
+/* Create a plan for one problem shape.
+ *   out    : receives the plan (set to NULL on failure).
+ *   ndim   : 1, 2 or 3.
+ *   shape  : ndim extents, each >= 1.
+ *   k      : ndim window sizes, each >= 1 (the contiguous dimension's window
+ *            k[ndim-1] must be <= 31 for 2-D/3-D).
+ *   stride : ndim steps >= 1, or NULL for all ones.
+ *   dtype  : SWCORR_U16 or SWCORR_F32 (x and y share it).
+ *   border : SWCORR_BORDER_CLIP.
+ *   flags  : SWCORR_FLAG_* bits.
+ * Host-only work plus device attribute queries; no kernel is launched. */
+swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shape,
+                                 const int32_t* k, const int32_t* stride, swcorr_dtype dtype,
+                                 swcorr_border border, uint32_t flags);
+
+/* Queue the correlation of device buffers x, y into device buffer c.
+ *   x, y      : device pointers, 16-byte aligned, plan dtype.
+ *   in_pitch  : ndim element pitches for x and y, or NULL (contiguous); the
+ *               byte pitch of every outer dimension must be a multiple of 16.
+ *   c         : device float32 output, ceil(shape[d]/stride[d]) per dim.
+ *   out_pitch : ndim element pitches for c, or NULL (contiguous).
+ *   sums      : device int64 buffer of 5 * (number of outputs) entries when the
+ *               plan has SWCORR_FLAG_EMIT_SUMS, else NULL.
+ *   stream    : cudaStream_t.
+ * Returns after queuing (asynchronous). */
+swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int64_t* in_pitch,
+                         float* c, const int64_t* out_pitch, int64_t* sums, void* stream);
+
+/* Same computation from HOST buffers: copies x and y to plan-owned device
+ * staging buffers, runs, copies c back and synchronises the stream.  Host
+ * buffers are contiguous; pinned memory gives the fastest copies.  The plan
+ * allocates its staging buffers on the first call (SWCORR_ERR_OOM on failure). */
+swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream);
+
+/* One scene of a batched plan.  Scenes are 2-D uint16 with square or
+ * rectangular windows (k[0] rows, k[1] cols, k[1] <= 31) and stride 1 in this
+ * version.  Pointers are device pointers that must stay valid for every
+ * swcorr_run_batched call on the plan. */
+typedef struct {
+  int64_t shape[2];     /* rows, cols */
+  int32_t k[2];         /* window rows, cols */
+  const void* x;        /* device, 16-byte aligned */
+  const void* y;        /* device, 16-byte aligned */
+  int64_t in_pitch;     /* elements between rows of x and y (>= cols, multiple of 8) */
+  float* c;             /* device output, rows x cols */
+  int64_t out_pitch;    /* elements between rows of c (>= cols) */
+} swcorr_scene;
+
+/* Plan one persistent launch over all scenes' tiles (a work queue ordered
+ * largest-cost first), captured in a CUDA graph on first run.  Copies the
+ * scene table; dtype must be SWCORR_U16. */
+swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
+                                  swcorr_dtype dtype, uint32_t flags);
+
+/* Launch the batched plan on a stream (graph launch). */
+swcorr_status swcorr_run_batched(swcorr_plan p, void* stream);
+
+/* Device-side status latched by the plan's kernels (read after the stream
+ * has synchronised; reading resets it).  SWCORR_OK if nothing went wrong. */
+swcorr_status swcorr_plan_status(swcorr_plan p);
+
+/* Number of output windows the plan computes per run. */
+int64_t swcorr_plan_outputs(swcorr_plan p);
+
+/* Release a plan (NULL is ignored).  Waits for nothing: the caller must have
+ * synchronised the streams the plan ran on. */
+void swcorr_plan_destroy(swcorr_plan p);
+
+const char* swcorr_status_string(swcorr_status s);
+
+/* Detail text of the last failing call on this thread ("" if none). */
+const char* swcorr_last_error(void);
+
+/* Library version, e.g. "swcorr 0.1.0 sm_103a". */
+const char* swcorr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWCORR_H */
