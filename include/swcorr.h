@@ -151,6 +151,11 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream);
  * has synchronised; reading resets it).  SWCORR_OK if nothing went wrong. */
 swcorr_status swcorr_plan_status(swcorr_plan p);
 
+/* Diagnostic: number of windows the plan's kernels recomputed through the
+ * exact per-window path (uint16 windows whose second-moment sums could not be
+ * certified below 2^32) since the last call; reading resets it.  -1 on error. */
+int64_t swcorr_plan_fallbacks(swcorr_plan p);
+
 /* Number of output windows the plan computes per run. */
 int64_t swcorr_plan_outputs(swcorr_plan p);
 

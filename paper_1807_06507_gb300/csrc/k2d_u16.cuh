@@ -1,0 +1,337 @@
+// k2d_u16.cuh -- fused 2-D sliding-window correlation for uint16 grids.
+//
+// Steps 1-4 of the optimized algorithm (Poyda & Zhizhin, Section 1) in one
+// pass over HBM, for one work item = (column strip of 32*M centre columns)
+// x (TJ output rows), processed by one warp:
+//
+//  * Rows stream into a shared-memory ring by TMA (one 2-D box row per
+//    input row, zero fill outside the grid = the clipped border).
+//  * Step 1 (products) is formed on the fly from the entering row e and the
+//    leaving row l = e - kh of each column: d = x_e - x_l, s = x_e + x_l,
+//    x_e^2 - x_l^2 = d*s, x_e y_e - x_l y_l = d_x y_e + x_l d_y.
+//  * Step 2 (row pass, window kw): in-lane prefix sums of those differences
+//    over the lane's M + kw - 1 columns; a window is a prefix difference.
+//  * Step 3 (column pass, window kh): register-resident running sums V, one
+//    per output column, updated by the row-pass difference of each new row.
+//  * Step 4: Pearson from the sums (Eq. 2), stored as float32.
+//
+// All sums are kept modulo 2^32, which is exact for sum x and sum y (at most
+// 961 * 65535 < 2^26) and exact for the second-moment sums whenever they are
+// below 2^32.  That is certified per window by M_w * Sx < 2^32 and
+// M_w * Sy < 2^32, with M_w an upper bound of the window's values (the
+// running maximum of the rows seen in this item): then sum x^2 <= M_w * Sx.
+// A window that fails the certificate (possible only for very bright, wide
+// windows) is recomputed exactly from shared memory in int64.
+//
+// Finalize, exact up to the last float32 roundings: with a = an integer near
+// the window mean and r = Sx - n a,
+//     T_x = sum (x - a)^2 = Sxx - a (Sx + r),   n Sxx - Sx^2 = n T_x - r^2,
+// and the same for y and for the cross term U = Sxy - b Sx - a s,
+// n Sxy - Sx Sy = n U - r s.  T_x, T_y < 2^32 and |U| < 2^31 (checked), so
+// they are exact in uint32 arithmetic; each Pearson factor is then one fused
+// multiply-add in float32.  A zero variance is detected exactly.
+#pragma once
+
+#include "common.cuh"
+#include "kparams.h"
+
+namespace swc {
+
+template <int M, int KW>
+struct Geo2D {
+  static constexpr int W1 = (KW - 1) / 2;         // window columns left of the centre
+  static constexpr int W2 = KW / 2;               // ... right of the centre
+  static constexpr int HALO = (W1 <= 8 && W2 <= 8) ? 8 : 16;
+  static constexpr int RW = 32 * M + 2 * HALO;    // elements loaded per row and channel
+  // TMA writes must start on 128-byte boundaries: ring rows are padded to a
+  // multiple of 64 elements and a row is loaded as NMAIN boxes of 256
+  // elements plus one TAIL box (both 128-byte aligned in shared memory).
+  static constexpr int RWS = (RW + 63) / 64 * 64; // ring row stride (elements)
+  static constexpr int NMAIN = RW / 256;
+  static constexpr int TAIL = RW - 256 * NMAIN;
+  static constexpr int OFF = HALO - W1;           // first needed element, from the lane base
+  static constexpr int CH0 = OFF / 8;             // first 16-byte chunk, from the lane base
+  static constexpr int E0 = OFF % 8;              // element offset inside that chunk
+  static constexpr int NCOL = M + KW - 1;         // columns each lane sums
+  static constexpr int NCH = (E0 + NCOL + 7) / 8; // 16-byte chunks per lane, row and channel
+  static constexpr int NWORD = 4 * NCH;
+  static_assert(TAIL % 8 == 0 && NMAIN >= 1, "row span cannot be split into TMA boxes");
+  static_assert(M % 8 == 0, "lane base must be 16-byte aligned");
+  static_assert(KW >= 1 && KW <= 31, "kw out of range");
+};
+
+struct Ring2D {
+  uint16_t* rx;  // [NR][RWS]
+  uint16_t* ry;  // [NR][RWS]
+  uint64_t* bar; // [NR]
+  int NR;
+  int PF;
+};
+
+__device__ __forceinline__ uint32_t get16(const uint32_t* w, int idx) {
+  const uint32_t v = w[idx >> 1];
+  return (idx & 1) ? (v >> 16) : (v & 0xFFFFu);
+}
+
+// Exact per-window recomputation (rare path): int64 sums over the window's
+// cells in the ring (cells outside the grid are zero there), Pearson in fp64.
+template <int M, int KW>
+__device__ __noinline__ float exact_window_u16(const Ring2D& rg, uint32_t q, int kh, int lane, int c, int n,
+                                               long long* out5) {
+  using G = Geo2D<M, KW>;
+  long long sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+  for (int r = 0; r < kh; r++) {
+    const uint32_t slot = (q - (uint32_t)(kh - 1) + (uint32_t)r) % (uint32_t)rg.NR;
+    const uint16_t* px = rg.rx + (size_t)slot * G::RWS + M * lane + G::HALO + c - G::W1;
+    const uint16_t* py = rg.ry + (size_t)slot * G::RWS + M * lane + G::HALO + c - G::W1;
+    for (int u = 0; u < KW; u++) {
+      const long long a = px[u], b = py[u];
+      sx += a;
+      sy += b;
+      sxx += a * a;
+      syy += b * b;
+      sxy += a * b;
+    }
+  }
+  if (out5) {
+    out5[0] = sx; out5[1] = sy; out5[2] = sxx; out5[3] = syy; out5[4] = sxy;
+  }
+  const long long vx = (long long)n * sxx - sx * sx;
+  const long long vy = (long long)n * syy - sy * sy;
+  const long long num = (long long)n * sxy - sx * sy;
+  if (vx == 0 || vy == 0) return __int_as_float(0x7fc00000);
+  double cc = (double)num / sqrt((double)vx * (double)vy);
+  cc = fmin(fmax(cc, -1.0), 1.0);
+  return (float)cc;
+}
+
+// Plain-load row loader (for row pitches that are not a multiple of 16 bytes,
+// which TMA cannot describe): the warp copies one input row span into a ring
+// slot, writing zeros outside the grid exactly as the TMA zero fill does.
+template <int RW>
+__device__ __forceinline__ void ldg_row_u16(uint16_t* dst, const uint16_t* src, long long pitch, int row, int xs,
+                                            int H, int W, int lane) {
+  const bool row_ok = row >= 0 && row < H;
+  const uint16_t* r = src + (long long)(row_ok ? row : 0) * pitch;
+  for (int e = lane; e < RW; e += 32) {
+    const int col = xs + e;
+    dst[e] = (row_ok && col >= 0 && col < W) ? __ldg(r + col) : (uint16_t)0;
+  }
+}
+
+// Process one work item.  Returns false if a bounded wait gave up (the
+// caller must then exit; in-flight copies have been drained).
+template <int M, int KW, bool TMA>
+__device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip, int rb, const Ring2D& rg,
+                                                    uint32_t& seq, uint32_t* status) {
+  using G = Geo2D<M, KW>;
+  const int lane = threadIdx.x & 31;
+  const int j0 = rb * sc.TJ;
+  const int j1 = min(j0 + sc.TJ, sc.OH);
+  const int t0 = j0 * sc.sy - sc.h1;
+  const int nrows = (j1 - 1 - j0) * sc.sy + sc.kh;
+  const int cstrip = strip * 32 * M;
+  const int xs = cstrip - G::HALO;
+  const uint32_t NR = (uint32_t)rg.NR;
+  const int PF = rg.PF;
+
+  auto issue = [&](int i) {
+    const uint32_t s = (seq + (uint32_t)i) % NR;
+    if (!TMA) {
+      ldg_row_u16<G::RW>(rg.rx + (size_t)s * G::RWS, (const uint16_t*)sc.gx, sc.in_pitch, t0 + i, xs, sc.H, sc.W,
+                         lane);
+      ldg_row_u16<G::RW>(rg.ry + (size_t)s * G::RWS, (const uint16_t*)sc.gy, sc.in_pitch, t0 + i, xs, sc.H, sc.W,
+                         lane);
+      return;
+    }
+    uint64_t* b = rg.bar + s;
+    mbar_arrive_expect_tx(b, 2u * G::RW * 2u);
+#pragma unroll
+    for (int q = 0; q < G::NMAIN; q++) {
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, t0 + i, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, t0 + i, b);
+    }
+    if (G::TAIL > 0) {
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, t0 + i, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, t0 + i, b);
+    }
+  };
+  if (TMA) {
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      const int npre = min(PF, nrows);
+      for (int i = 0; i < npre; i++) issue(i);
+    }
+  } else {
+    const int npre = min(PF, nrows);
+    for (int i = 0; i < npre; i++) issue(i);
+  }
+
+  // Lane geometry: centre columns [cl, cl + M); interior if its whole block
+  // of columns lies inside the grid.
+  const int cl = cstrip + M * lane;
+  const bool col_interior = (cl - G::W1 >= 0) && (cl + M - 1 + G::W2 <= sc.W - 1);
+  const uint32_t n_int = (uint32_t)(sc.kh * KW);
+  const float fn_int = (float)n_int;
+
+  uint32_t V[M][5];
+#pragma unroll
+  for (int c = 0; c < M; c++)
+#pragma unroll
+    for (int k = 0; k < 5; k++) V[c][k] = 0u;
+  uint32_t mx2 = 0u, my2 = 0u;
+
+  for (int i = 0; i < nrows; i++) {
+    __syncwarp();
+    if (TMA) {
+      if (lane == 0 && i + PF < nrows) {
+        fence_proxy_async_smem();
+        issue(i + PF);
+      }
+    } else if (i + PF < nrows) {
+      issue(i + PF);
+    }
+    const uint32_t q = seq + (uint32_t)i;
+    const uint32_t s = q % NR;
+    if (!TMA) {
+      __syncwarp();
+    } else if (!mbar_wait_bounded(rg.bar + s, (q / NR) & 1u, status)) {
+      // drain every copy still in flight into this CTA's ring, then give up
+      const int last = min(i + PF, nrows);
+      for (int k = i + 1; k < last; k++) {
+        const uint32_t qk = seq + (uint32_t)k;
+        mbar_wait_bounded(rg.bar + qk % NR, (qk / NR) & 1u, status);
+      }
+      return false;
+    }
+    const bool has_leave = i >= sc.kh;
+    const uint32_t sl = (q + NR - (uint32_t)sc.kh % NR) % NR;
+
+    uint32_t we[G::NWORD], wl[G::NWORD], ye[G::NWORD], yl[G::NWORD];
+    {
+      const uint16_t* pe = rg.rx + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
+      const uint16_t* qe = rg.ry + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
+#pragma unroll
+      for (int h = 0; h < G::NCH; h++) {
+        const uint4 a = *reinterpret_cast<const uint4*>(pe + 8 * h);
+        const uint4 b = *reinterpret_cast<const uint4*>(qe + 8 * h);
+        we[4 * h] = a.x; we[4 * h + 1] = a.y; we[4 * h + 2] = a.z; we[4 * h + 3] = a.w;
+        ye[4 * h] = b.x; ye[4 * h + 1] = b.y; ye[4 * h + 2] = b.z; ye[4 * h + 3] = b.w;
+      }
+      if (has_leave) {
+        const uint16_t* pl = rg.rx + (size_t)sl * G::RWS + M * lane + G::CH0 * 8;
+        const uint16_t* ql = rg.ry + (size_t)sl * G::RWS + M * lane + G::CH0 * 8;
+#pragma unroll
+        for (int h = 0; h < G::NCH; h++) {
+          const uint4 a = *reinterpret_cast<const uint4*>(pl + 8 * h);
+          const uint4 b = *reinterpret_cast<const uint4*>(ql + 8 * h);
+          wl[4 * h] = a.x; wl[4 * h + 1] = a.y; wl[4 * h + 2] = a.z; wl[4 * h + 3] = a.w;
+          yl[4 * h] = b.x; yl[4 * h + 1] = b.y; yl[4 * h + 2] = b.z; yl[4 * h + 3] = b.w;
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < G::NWORD; w++) { wl[w] = 0u; yl[w] = 0u; }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < G::NWORD; w++) {
+      mx2 = __vmaxu2(mx2, we[w]);
+      my2 = __vmaxu2(my2, ye[w]);
+    }
+
+    // Row pass on the entering-minus-leaving differences, then the running
+    // column sums.
+    uint32_t P[5] = {0u, 0u, 0u, 0u, 0u};
+    uint32_t Pst[M][5];  // prefix after column e, kept for output e + 1
+#pragma unroll
+    for (int e = 0; e < G::NCOL; e++) {
+      const uint32_t xe = get16(we, G::E0 + e), xl = get16(wl, G::E0 + e);
+      const uint32_t yv = get16(ye, G::E0 + e), ylv = get16(yl, G::E0 + e);
+      const uint32_t dx = xe - xl, sxs = xe + xl;
+      const uint32_t dy = yv - ylv, sys = yv + ylv;
+      P[0] += dx;
+      P[1] += dy;
+      P[2] += dx * sxs;
+      P[3] += dy * sys;
+      P[4] += dx * yv + xl * dy;
+      if (e >= KW - 1) {
+        const int c = e - (KW - 1);
+#pragma unroll
+        for (int k = 0; k < 5; k++) V[c][k] += P[k] - (c >= 1 ? Pst[c - 1][k] : 0u);
+      }
+      if (e <= M - 2) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) Pst[e][k] = P[k];
+      }
+    }
+
+    // Step 4 for the output row whose window is now complete.
+    const int rc = t0 + i - sc.h2;
+    if (i >= sc.kh - 1 && (rc % sc.sy) == 0) {
+      const int jr = rc / sc.sy;
+      const int cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
+      const bool interior = col_interior && (cnt_r == sc.kh);
+      const uint32_t Mx = max(mx2 & 0xFFFFu, mx2 >> 16), My = max(my2 & 0xFFFFu, my2 >> 16);
+      float res[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        const uint32_t Sx = V[c][0], Sy = V[c][1], Sxx = V[c][2], Syy = V[c][3], Sxy = V[c][4];
+        uint32_t n, a, b;
+        float fn;
+        if (interior) {
+          n = n_int;
+          fn = fn_int;
+          a = __umulhi(Sx, sc.inv_n);
+          b = __umulhi(Sy, sc.inv_n);
+        } else {
+          const int cc = cl + c;
+          const int cnt_c = min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1;
+          n = (uint32_t)(cnt_r * max(cnt_c, 1));
+          fn = (float)n;
+          const float rn = 1.0f / fn;
+          a = (uint32_t)((float)Sx * rn);
+          b = (uint32_t)((float)Sy * rn);
+        }
+        const int r = (int)(Sx - n * a), s2 = (int)(Sy - n * b);
+        const uint32_t Tx = Sxx - a * (Sx + (uint32_t)r);
+        const uint32_t Ty = Syy - b * (Sy + (uint32_t)s2);
+        const int U = (int)(Sxy - b * Sx - a * (uint32_t)s2);
+        const float fTx = (float)Tx, fTy = (float)Ty;
+        const float fr = (float)r, fs = (float)s2;
+        const float vx = fmaf(fn, fTx, -fr * fr);
+        const float vy = fmaf(fn, fTy, -fs * fs);
+        const float num = fmaf(fn, (float)U, -fr * fs);
+        float cv = num * rsqrtf(vx * vy);
+        cv = fminf(fmaxf(cv, -1.0f), 1.0f);
+        if (vx == 0.0f || vy == 0.0f) cv = __int_as_float(0x7fc00000);
+        const bool cert = (__umulhi(Mx, Sx) == 0u) && (__umulhi(My, Sy) == 0u) && (fTx * fTy < 4.0e18f);
+        const int cc = cl + c;
+        long long* s5 = nullptr;
+        if (sc.sums && cc < sc.W && (cc % sc.sx) == 0)
+          s5 = sc.sums + 5ll * ((long long)jr * sc.OW + cc / sc.sx);
+        if (!cert) {
+          cv = exact_window_u16<M, KW>(rg, q, sc.kh, lane, c, (int)n, s5);
+          atomicAdd(status + ST_FALLBACK, 1u);
+        } else if (s5) {
+          s5[0] = Sx; s5[1] = Sy; s5[2] = Sxx; s5[3] = Syy; s5[4] = Sxy;
+        }
+        res[c] = cv;
+      }
+      float* orow = sc.out + (long long)jr * sc.out_pitch;
+      if (sc.vec_store && cl + M <= sc.W) {
+#pragma unroll
+        for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const int cc = cl + c;
+          if (cc < sc.W && (cc % sc.sx) == 0) orow[cc / sc.sx] = res[c];
+        }
+      }
+    }
+  }
+  seq += (uint32_t)nrows;
+  return true;
+}
+
+}  // namespace swc

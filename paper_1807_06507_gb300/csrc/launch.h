@@ -1,0 +1,19 @@
+// launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kparams.h"
+
+namespace swc {
+
+struct Geo2DInfo {
+  int M, KW, HALO, RW, RWS, TAIL;
+};
+
+// 2-D uint16: geometry of the instance that serves window width kw (false if
+// kw has no instance) and its launch.
+bool k2d_u16_geometry(int kw, Geo2DInfo* g);
+cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+
+}  // namespace swc

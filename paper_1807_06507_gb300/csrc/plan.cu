@@ -1,0 +1,398 @@
+// plan.cu -- host side of libswcorr: argument validation, plans, TMA tensor
+// maps, launches and the C ABI declared in include/swcorr.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/swcorr.h"
+#include "launch.h"
+
+using namespace swc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+swcorr_status fail(swcorr_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+swcorr_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SWCORR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda
+// link dependency).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+swcorr_status encode_2d(CUtensorMap* m, CUtensorMapDataType dt, int elem_bytes, const void* base, int64_t W,
+                        int64_t H, int64_t pitch_elems, int box_w) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, 1u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return SWCORR_OK;
+}
+
+struct DeviceInfo {
+  int dev = -1;
+  int sms = 0;
+  int smem_optin = 0;
+  int cc_major = 0, cc_minor = 0;
+};
+
+swcorr_status device_info(DeviceInfo* d) {
+  cudaError_t e = cudaGetDevice(&d->dev);
+  if (e != cudaSuccess) return fail(SWCORR_ERR_NO_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+  cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, d->dev);
+  cudaDeviceGetAttribute(&d->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->dev);
+  cudaDeviceGetAttribute(&d->cc_major, cudaDevAttrComputeCapabilityMajor, d->dev);
+  cudaDeviceGetAttribute(&d->cc_minor, cudaDevAttrComputeCapabilityMinor, d->dev);
+  if (d->cc_major != 10 || d->cc_minor != 3)
+    return fail(SWCORR_ERR_NO_DEVICE, "libswcorr is built for sm_103a; device %d is sm_%d%d", d->dev, d->cc_major,
+                d->cc_minor);
+  return SWCORR_OK;
+}
+
+}  // namespace
+
+enum PlanKind { KIND_2D_U16 = 1, KIND_BATCHED = 10 };
+
+struct swcorr_plan_s {
+  int kind = 0;
+  int ndim = 0;
+  int64_t shape[3] = {1, 1, 1};
+  int32_t k[3] = {1, 1, 1};
+  int32_t stride[3] = {1, 1, 1};
+  int64_t oshape[3] = {1, 1, 1};
+  swcorr_dtype dtype = SWCORR_U16;
+  uint32_t flags = 0;
+  DeviceInfo dev;
+  // 2-D geometry and launch shape
+  Geo2DInfo g2{};
+  K2DParams k2{};
+  int grid = 0;
+  size_t smem = 0;
+  // tensor-map cache
+  const void* cached_x = nullptr;
+  const void* cached_y = nullptr;
+  int64_t cached_pitch = -1;
+  // device status block
+  uint32_t* d_status = nullptr;
+  // staging for host runs
+  void* d_x = nullptr;
+  void* d_y = nullptr;
+  float* d_c = nullptr;
+};
+
+static int64_t n_outputs(const swcorr_plan_s* p) {
+  int64_t n = 1;
+  for (int d = 0; d < p->ndim; d++) n *= p->oshape[d];
+  return n;
+}
+
+static size_t elem_size(swcorr_dtype dt) { return dt == SWCORR_U16 ? 2 : 4; }
+
+static swcorr_status plan_2d_u16(swcorr_plan_s* p) {
+  const int H = (int)p->shape[0], W = (int)p->shape[1];
+  const int kh = p->k[0], kw = p->k[1];
+  if (!k2d_u16_geometry(kw, &p->g2))
+    return fail(SWCORR_ERR_UNSUPPORTED, "2-D uint16: window width %d has no kernel instance (1..31 odd)", kw);
+  const Geo2DInfo& g = p->g2;
+  Scene2D& sc = p->k2.sc;
+  sc.H = H;
+  sc.W = W;
+  sc.kh = kh;
+  sc.h1 = (kh - 1) / 2;
+  sc.h2 = kh / 2;
+  sc.kw = kw;
+  sc.sy = p->stride[0];
+  sc.sx = p->stride[1];
+  sc.OH = (int)p->oshape[0];
+  sc.OW = (int)p->oshape[1];
+  sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
+  const uint64_t n = (uint64_t)kh * (uint64_t)kw;
+  sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
+  const int PF = 8;
+  const int NR = kh + 1 + PF;
+  p->k2.NR = NR;
+  p->k2.PF = PF;
+  p->smem = (size_t)NR * g.RWS * 2 * 2 + (size_t)NR * 8;
+  if (p->smem > (size_t)p->dev.smem_optin)
+    return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, p->smem);
+  // one wave of work items over the resident warps
+  const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / (p->smem + 1024))));
+  const int total = p->dev.sms * per_sm;
+  int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
+  TJ = std::max(TJ, std::max(16, 4 * kh / std::max(1, sc.sy)));
+  TJ = std::min(TJ, sc.OH);
+  sc.TJ = TJ;
+  sc.n_rb = (sc.OH + TJ - 1) / TJ;
+  p->k2.n_items = sc.n_rb * sc.n_strips;
+  p->grid = std::min(p->k2.n_items, total);
+  return SWCORR_OK;
+}
+
+extern "C" {
+
+const char* swcorr_status_string(swcorr_status s) {
+  switch (s) {
+    case SWCORR_OK: return "ok";
+    case SWCORR_ERR_INVALID_ARG: return "invalid argument";
+    case SWCORR_ERR_UNSUPPORTED: return "unsupported";
+    case SWCORR_ERR_ALIGNMENT: return "alignment";
+    case SWCORR_ERR_CUDA: return "CUDA error";
+    case SWCORR_ERR_OOM: return "out of memory";
+    case SWCORR_ERR_TIMEOUT: return "device wait timed out";
+    case SWCORR_ERR_NO_DEVICE: return "no usable device";
+  }
+  return "unknown status";
+}
+
+const char* swcorr_last_error(void) { return g_last_error.c_str(); }
+
+const char* swcorr_version(void) { return "swcorr 0.1.0 sm_103a"; }
+
+swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shape, const int32_t* k,
+                                 const int32_t* stride, swcorr_dtype dtype, swcorr_border border, uint32_t flags) {
+  g_last_error.clear();
+  if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3) return fail(SWCORR_ERR_UNSUPPORTED, "ndim must be 1, 2 or 3 (got %d)", ndim);
+  if (!shape || !k) return fail(SWCORR_ERR_INVALID_ARG, "shape and k must not be NULL");
+  if (dtype != SWCORR_U16 && dtype != SWCORR_F32) return fail(SWCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  if (border != SWCORR_BORDER_CLIP) return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
+  if (flags & ~(uint32_t)SWCORR_FLAG_EMIT_SUMS) return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
+  if ((flags & SWCORR_FLAG_EMIT_SUMS) && dtype != SWCORR_U16)
+    return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_EMIT_SUMS needs uint16 data");
+  swcorr_plan_s tmp;
+  tmp.ndim = ndim;
+  tmp.dtype = dtype;
+  tmp.flags = flags;
+  for (int d = 0; d < ndim; d++) {
+    if (shape[d] < 1) return fail(SWCORR_ERR_INVALID_ARG, "shape[%d] = %lld < 1", d, (long long)shape[d]);
+    if (shape[d] > (1ll << 31) - 1024) return fail(SWCORR_ERR_UNSUPPORTED, "shape[%d] too large", d);
+    if (k[d] < 1) return fail(SWCORR_ERR_INVALID_ARG, "k[%d] = %d < 1", d, k[d]);
+    const int32_t s = stride ? stride[d] : 1;
+    if (s < 1) return fail(SWCORR_ERR_INVALID_ARG, "stride[%d] = %d < 1", d, s);
+    tmp.shape[d] = shape[d];
+    tmp.k[d] = k[d];
+    tmp.stride[d] = s;
+    tmp.oshape[d] = (shape[d] + s - 1) / s;
+  }
+  swcorr_status st = device_info(&tmp.dev);
+  if (st != SWCORR_OK) return st;
+  if (ndim == 2 && dtype == SWCORR_U16) {
+    tmp.kind = KIND_2D_U16;
+    st = plan_2d_u16(&tmp);
+  } else {
+    st = fail(SWCORR_ERR_UNSUPPORTED, "ndim %d with dtype %s is not provided yet", ndim,
+              dtype == SWCORR_U16 ? "u16" : "f32");
+  }
+  if (st != SWCORR_OK) return st;
+  swcorr_plan_s* p = new (std::nothrow) swcorr_plan_s(tmp);
+  if (!p) return fail(SWCORR_ERR_OOM, "host allocation of the plan failed");
+  cudaError_t e = cudaMalloc(&p->d_status, ST_WORDS * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    delete p;
+    return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "status block: out of device memory")
+                                          : cuda_fail(e, "cudaMalloc(status)");
+  }
+  e = cudaMemset(p->d_status, 0, ST_WORDS * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    cudaFree(p->d_status);
+    delete p;
+    return cuda_fail(e, "cudaMemset(status)");
+  }
+  p->k2.status = p->d_status;
+  *out = p;
+  return SWCORR_OK;
+}
+
+int64_t swcorr_plan_outputs(swcorr_plan p) { return p ? n_outputs(p) : -1; }
+
+static swcorr_status run_2d_u16(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                                const int64_t* out_pitch, int64_t* sums, cudaStream_t st) {
+  const int64_t W = p->shape[1], H = p->shape[0];
+  const int64_t ip = in_pitch ? in_pitch[0] : W;
+  if (in_pitch && in_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[1] must be 1");
+  if (ip < W) return fail(SWCORR_ERR_INVALID_ARG, "in_pitch[0] = %lld < cols = %lld", (long long)ip, (long long)W);
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 1)
+    return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
+  const bool base_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  // TMA needs 16-byte aligned bases and row pitches; anything else takes the
+  // plain-load row loader (same kernel, same results).
+  const bool tma = (ip * 2) % 16 == 0;
+  const int64_t op = out_pitch ? out_pitch[0] : p->oshape[1];
+  if (out_pitch && out_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "out_pitch[1] must be 1");
+  if (op < p->oshape[1]) return fail(SWCORR_ERR_INVALID_ARG, "out_pitch[0] smaller than the output row");
+  const bool use_tma = tma && base_ok;
+  if (use_tma && (x != p->cached_x || y != p->cached_y || ip != p->cached_pitch)) {
+    swcorr_status s1 = encode_2d(&p->k2.tmx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, 256);
+    if (s1 == SWCORR_OK) s1 = encode_2d(&p->k2.tmy, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, 256);
+    if (s1 == SWCORR_OK && p->g2.TAIL > 0) {
+      s1 = encode_2d(&p->k2.tmx_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, p->g2.TAIL);
+      if (s1 == SWCORR_OK) s1 = encode_2d(&p->k2.tmy_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, p->g2.TAIL);
+    }
+    if (s1 != SWCORR_OK) {
+      p->cached_x = p->cached_y = nullptr;
+      return s1;
+    }
+    p->cached_x = x;
+    p->cached_y = y;
+    p->cached_pitch = ip;
+  }
+  Scene2D& sc = p->k2.sc;
+  sc.gx = x;
+  sc.gy = y;
+  sc.in_pitch = ip;
+  sc.out = c;
+  sc.out_pitch = op;
+  sc.sums = reinterpret_cast<long long*>(sums);
+  sc.vec_store = (sc.sx == 1 && (reinterpret_cast<uintptr_t>(c) & 15) == 0 && (op % 4) == 0) ? 1 : 0;
+  cudaError_t e = k2d_u16_launch(sc.kw, p->k2, p->grid, p->smem, st, use_tma);
+  if (e != cudaSuccess) return cuda_fail(e, "2-D uint16 kernel launch");
+  return SWCORR_OK;
+}
+
+swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                         const int64_t* out_pitch, int64_t* sums, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
+  if (p->kind == KIND_BATCHED) return fail(SWCORR_ERR_INVALID_ARG, "batched plans run with swcorr_run_batched");
+  if (!x || !y || !c) return fail(SWCORR_ERR_INVALID_ARG, "x, y and c must not be NULL");
+  if ((p->flags & SWCORR_FLAG_EMIT_SUMS) && !sums)
+    return fail(SWCORR_ERR_INVALID_ARG, "plan has SWCORR_FLAG_EMIT_SUMS: sums must not be NULL");
+  if (!(p->flags & SWCORR_FLAG_EMIT_SUMS)) sums = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  switch (p->kind) {
+    case KIND_2D_U16: return run_2d_u16(p, x, y, in_pitch, c, out_pitch, sums, st);
+  }
+  return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);
+}
+
+swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
+  if (!x || !y || !c) return fail(SWCORR_ERR_INVALID_ARG, "x, y and c must not be NULL");
+  if (p->kind == KIND_BATCHED) return fail(SWCORR_ERR_INVALID_ARG, "batched plans have no host run");
+  if (p->flags & SWCORR_FLAG_EMIT_SUMS) return fail(SWCORR_ERR_INVALID_ARG, "host runs do not emit sums");
+  int64_t nin = 1;
+  for (int d = 0; d < p->ndim; d++) nin *= p->shape[d];
+  const size_t in_bytes = (size_t)nin * elem_size(p->dtype);
+  const size_t out_bytes = (size_t)n_outputs(p) * sizeof(float);
+  cudaError_t e;
+  if (!p->d_x) {
+    // rows padded to 16 bytes so the device copy satisfies the TMA pitch rule
+    if ((e = cudaMalloc(&p->d_x, in_bytes + 64)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_y, in_bytes + 64)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_c, out_bytes + 64)) != cudaSuccess) {
+      cudaFree(p->d_x);
+      cudaFree(p->d_y);
+      cudaFree(p->d_c);
+      p->d_x = p->d_y = nullptr;
+      p->d_c = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "staging buffers: out of device memory")
+                                            : cuda_fail(e, "cudaMalloc(staging)");
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t inner = p->shape[p->ndim - 1];
+  if (p->ndim >= 2 && (inner * (int64_t)elem_size(p->dtype)) % 16 != 0)
+    return fail(SWCORR_ERR_ALIGNMENT, "host runs need rows of a multiple of 16 bytes (got %lld elements)",
+                (long long)inner);
+  if ((e = cudaMemcpyAsync(p->d_x, x, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "copy x to device");
+  if ((e = cudaMemcpyAsync(p->d_y, y, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "copy y to device");
+  swcorr_status s = swcorr_run(p, p->d_x, p->d_y, nullptr, p->d_c, nullptr, nullptr, stream);
+  if (s != SWCORR_OK) return s;
+  if ((e = cudaMemcpyAsync(c, p->d_c, out_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "copy c to host");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return SWCORR_OK;
+}
+
+swcorr_status swcorr_plan_status(swcorr_plan p) {
+  g_last_error.clear();
+  if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
+  uint32_t h[ST_WORDS];
+  cudaError_t e = cudaMemcpy(h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status block");
+  uint32_t zero = 0;
+  cudaMemcpy(p->d_status + ST_ERROR, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  if (h[ST_ERROR] & ERRBIT_TIMEOUT) return fail(SWCORR_ERR_TIMEOUT, "a kernel's bounded wait gave up");
+  if (h[ST_ERROR]) return fail(SWCORR_ERR_CUDA, "device status bits 0x%x", h[ST_ERROR]);
+  return SWCORR_OK;
+}
+
+int64_t swcorr_plan_fallbacks(swcorr_plan p) {
+  if (!p) return -1;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, p->d_status + ST_FALLBACK, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  uint32_t zero = 0;
+  cudaMemcpy(p->d_status + ST_FALLBACK, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  return v;
+}
+
+void swcorr_plan_destroy(swcorr_plan p) {
+  if (!p) return;
+  cudaFree(p->d_status);
+  cudaFree(p->d_x);
+  cudaFree(p->d_y);
+  cudaFree(p->d_c);
+  delete p;
+}
+
+swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes, swcorr_dtype dtype,
+                                  uint32_t flags) {
+  g_last_error.clear();
+  if (out) *out = nullptr;
+  (void)scenes;
+  (void)n_scenes;
+  (void)dtype;
+  (void)flags;
+  return fail(SWCORR_ERR_UNSUPPORTED, "batched plans are not provided yet");
+}
+
+swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
+  (void)stream;
+  if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
+  return fail(SWCORR_ERR_UNSUPPORTED, "batched plans are not provided yet");
+}
+
+}  // extern "C"

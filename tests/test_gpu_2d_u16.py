@@ -1,0 +1,160 @@
+"""GPU parity of the fused 2-D uint16 kernel against the CPU oracle.
+
+Calls go through the C ABI (ctypes binding).  The integer window sums are
+compared bit-exactly with the oracle's brute-force int64 sums; c within 1e-5
+on every finite window, with identical NaN masks (the zero-variance test is
+exact on both sides).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_06507_gb300 import workloads as W
+from tests.gpu_util import score, to_dev, sample_indices
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_1807_06507_gb300 import swcorr
+    swcorr.load()
+    return swcorr
+
+
+def run_u16(sw, x, y, k, stride=None, sums=False, **kw):
+    p = sw.Plan(x.shape, k, stride, dtype="u16", flags=sw.FLAG_EMIT_SUMS if sums else 0)
+    xd, yd = to_dev(x, torch), to_dev(y, torch)
+    s = torch.zeros(p.outputs() * 5, dtype=torch.int64, device="cuda") if sums else None
+    c = p.run(xd, yd, sums=s, **kw)
+    torch.cuda.synchronize()
+    p.check_status()
+    fb = p.fallbacks()
+    out = (c.cpu().numpy(), s.cpu().numpy().reshape(tuple(p.oshape) + (5,)) if sums else None, fb)
+    p.close()
+    return out
+
+
+@pytest.mark.parametrize("shape,k", [((257, 530), 7), ((100, 1100), 3), ((64, 97), 5), ((300, 515), 15),
+                                     ((200, 300), 31), ((41, 600), (7, 3)), ((90, 128), (3, 9)),
+                                     ((33, 40), (1, 7)), ((20, 530), (9, 1))])
+def test_night_scene_parity_and_exact_sums(sw, shape, k):
+    x, y = W.night_scene(shape, seed=W.seed_for(2) + shape[0])
+    c, s, _ = run_u16(sw, x, y, k, sums=True)
+    assert np.array_equal(s, oracle.sums_u16(x, y, k))
+    score(c, oracle.corr(x, y, k))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (3, 700), (700, 3), (5, 5), (2, 513), (17, 1025)])
+def test_tiny_and_ragged(sw, shape):
+    rng = np.random.default_rng(sum(shape))
+    x = rng.integers(0, 65536, shape).astype(np.uint16)
+    y = rng.integers(0, 65536, shape).astype(np.uint16)
+    for k in (1, 3, 7):
+        c, s, _ = run_u16(sw, x, y, k, sums=True)
+        assert np.array_equal(s, oracle.sums_u16(x, y, k))
+        score(c, oracle.corr(x, y, k))
+
+
+def test_full_range_forces_exact_fallback(sw):
+    # bright, wide windows: second moments beyond 2^32 must take the exact path
+    rng = np.random.default_rng(77)
+    x = rng.integers(40000, 65536, (120, 600)).astype(np.uint16)
+    y = rng.integers(0, 65536, (120, 600)).astype(np.uint16)
+    c, s, fb = run_u16(sw, x, y, 7, sums=True)
+    assert fb > 0
+    assert np.array_equal(s, oracle.sums_u16(x, y, 7))
+    score(c, oracle.corr(x, y, 7))
+
+
+@pytest.mark.parametrize("stride", [(2, 2), (3, 1), (1, 2), (2, 3)])
+def test_strides(sw, stride):
+    x, y = W.night_scene((123, 700), seed=5)
+    c, s, _ = run_u16(sw, x, y, 7, stride=stride, sums=True)
+    assert c.shape == (-(-123 // stride[0]), -(-700 // stride[1]))
+    assert np.array_equal(s, oracle.sums_u16(x, y, 7, stride))
+    score(c, oracle.corr(x, y, 7, stride))
+
+
+def test_constant_patches_are_nan(sw):
+    x, y = W.night_scene((150, 400), seed=9)
+    x[20:60, 30:200] = 4242
+    y[100:140, 100:390] = 0
+    c, _, _ = run_u16(sw, x, y, 7)
+    ref = oracle.corr(x, y, 7)
+    assert np.isnan(ref).sum() > 1000
+    score(c, ref)
+
+
+def test_pitched_input_and_output(sw):
+    x, y = W.night_scene((130, 500), seed=11)
+    xp = np.zeros((130, 520), np.uint16)
+    yp = np.zeros((130, 520), np.uint16)
+    xp[:, :500], yp[:, :500] = x, y
+    p = sw.Plan(x.shape, 7, dtype="u16")
+    xd, yd = to_dev(xp, torch), to_dev(yp, torch)
+    cbig = torch.full((130, 512), 7.0, dtype=torch.float32, device="cuda")
+    p.run(xd, yd, c=cbig, in_pitch=(520, 1), out_pitch=(512, 1))
+    torch.cuda.synchronize()
+    p.check_status()
+    cb = cbig.cpu().numpy()
+    assert np.all(cb[:, 500:] == 7.0)
+    score(cb[:, :500], oracle.corr(x, y, 7))
+
+
+def test_unaligned_pitch_uses_plain_loads(sw):
+    # a row pitch of 51 uint16 (102 B) cannot be described to TMA; the
+    # plain-load row loader must give the same results
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, 16384, (40, 51)).astype(np.uint16)
+    y = rng.integers(0, 16384, (40, 51)).astype(np.uint16)
+    c, s, _ = run_u16(sw, x, y, 5, sums=True)
+    assert np.array_equal(s, oracle.sums_u16(x, y, 5))
+    score(c, oracle.corr(x, y, 5))
+    xs, ys = x[:, :50], y[:, :50]
+    p = sw.Plan((40, 50), 5, dtype="u16")
+    cp = p.run(to_dev(x, torch), to_dev(y, torch), in_pitch=(51, 1))
+    torch.cuda.synchronize()
+    score(cp.cpu().numpy(), oracle.corr(np.ascontiguousarray(xs), np.ascontiguousarray(ys), 5))
+
+
+def test_odd_base_address_rejected(sw):
+    p = sw.Plan((10, 48), 3, dtype="u16")
+    buf = torch.zeros(10 * 48 * 2 + 16, dtype=torch.uint8, device="cuda")
+    c = torch.empty((10, 48), dtype=torch.float32, device="cuda")
+
+    class Odd:
+        def __init__(self, ptr):
+            self.ptr = ptr
+
+        def data_ptr(self):
+            return self.ptr
+
+        def is_contiguous(self):
+            return True
+
+        device = buf.device
+
+    with pytest.raises(sw.SwcorrError) as ei:
+        p.run(Odd(buf.data_ptr() + 1), Odd(buf.data_ptr() + 1), c=c)
+    assert ei.value.status == sw.ERR_ALIGNMENT
+
+
+def test_night_scene_full_size(sw):
+    # 12 Mpx night scene, 7x7: every window against the oracle.
+    x, y = W.night_scene((3000, 4000), seed=W.seed_for(2))
+    c, s, fb = run_u16(sw, x, y, 7, sums=True)
+    assert np.array_equal(s, oracle.sums_u16(x, y, 7))
+    m, n_sc, _ = score(c, oracle.corr(x, y, 7))
+    assert n_sc > 11_000_000
+
+
+def test_host_run_matches_device_run(sw):
+    x, y = W.night_scene((200, 640), seed=13)
+    p = sw.Plan(x.shape, 7, dtype="u16")
+    ch = p.run_host(x, y)
+    cd = p.run(to_dev(x, torch), to_dev(y, torch))
+    torch.cuda.synchronize()
+    assert np.array_equal(ch, cd.cpu().numpy(), equal_nan=True)
+    score(ch, oracle.corr(x, y, 7))
