@@ -290,7 +290,7 @@ def run_ours(args, world, rank, local):
                    "hbm_gbs_algorithmic": achieved, "max_abs_dc_sampled": max_dc},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k2d_u16_kernel<16,7>", "bytes_per_window": BYTES_PER_WINDOW_U16},
+                     "kernel": "k2d_u16_kernel<8,7,1>", "bytes_per_window": BYTES_PER_WINDOW_U16},
         "cpu_baseline": {"value": cpu_v, "unit": "windows/s", "cores": cpu_threads, "kind": "oracle",
                          "sample": cpu_sample},
         "e2e": {"value": e2e, "unit": "windows/s", "h2d_bytes_per_step": 2 * 2 * n_win,

@@ -70,7 +70,7 @@ static void geo(Geo2DInfo* g) {
   g->TAIL = G::TAIL;
 }
 
-#define SWC_K2D_CASES(X) X(16, 1) X(16, 3) X(16, 5) X(16, 7) X(16, 9) X(8, 11) X(8, 13) X(8, 15) X(8, 17) \
+#define SWC_K2D_CASES(X) X(8, 1) X(8, 3) X(8, 5) X(8, 7) X(8, 9) X(8, 11) X(8, 13) X(8, 15) X(8, 17) \
   X(8, 19) X(8, 21) X(8, 23) X(8, 25) X(8, 27) X(8, 29) X(8, 31)
 
 bool k2d_u16_geometry(int kw, Geo2DInfo* g) {

@@ -17,19 +17,21 @@
 //
 // All sums are kept modulo 2^32, which is exact for sum x and sum y (at most
 // 961 * 65535 < 2^26) and exact for the second-moment sums whenever they are
-// below 2^32.  That is certified per window by M_w * Sx < 2^32 and
-// M_w * Sy < 2^32, with M_w an upper bound of the window's values (the
-// running maximum of the rows seen in this item): then sum x^2 <= M_w * Sx.
-// A window that fails the certificate (possible only for very bright, wide
-// windows) is recomputed exactly from shared memory in int64.
+// below 2^32.  That is certified by M_w * Sx < 2^32 and M_w * Sy < 2^32,
+// with M_w an upper bound of the window's values (the running maximum of the
+// rows seen in this item): then sum x^2 <= M_w * Sx.  One test on the largest
+// Sx, Sy of a lane's row certifies all its windows at once; a window that
+// fails it (possible only for very bright, wide windows) is tested alone and,
+// if needed, recomputed exactly from shared memory in int64.
 //
 // Finalize, exact up to the last float32 roundings: with a = an integer near
 // the window mean and r = Sx - n a,
 //     T_x = sum (x - a)^2 = Sxx - a (Sx + r),   n Sxx - Sx^2 = n T_x - r^2,
 // and the same for y and for the cross term U = Sxy - b Sx - a s,
-// n Sxy - Sx Sy = n U - r s.  T_x, T_y < 2^32 and |U| < 2^31 (checked), so
-// they are exact in uint32 arithmetic; each Pearson factor is then one fused
-// multiply-add in float32.  A zero variance is detected exactly.
+// n Sxy - Sx Sy = n U - r s.  T_x, T_y < 2^32 (certified) and |U| < 2^31
+// (checked through T_x T_y < 2^62), so they are exact in 32-bit arithmetic;
+// each Pearson factor is then one fused multiply-add in float32.  A zero
+// variance is detected exactly.
 #pragma once
 
 #include "common.cuh"
@@ -119,6 +121,40 @@ __device__ __forceinline__ void ldg_row_u16(uint16_t* dst, const uint16_t* src, 
   }
 }
 
+// Float of a small signed integer (|v| < 2^22) on the FMA/ALU pipes.
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// Step 4 for one output from its exact modular window sums (see the file
+// header).  Valid when Sxx, Syy < 2^32 (certified by the caller) and
+// T_x T_y < 2^62, i.e. |U| < 2^31: the caller checks tt = T_x T_y.
+__device__ __forceinline__ float pearson_u16(uint32_t Sx, uint32_t Sy, uint32_t Sxx, uint32_t Syy, uint32_t Sxy,
+                                             uint32_t n, float fn, uint32_t a, uint32_t b, float& tt) {
+  const int r = (int)(Sx - n * a), s = (int)(Sy - n * b);
+  const uint32_t Tx = Sxx - a * (Sx + (uint32_t)r);
+  const uint32_t Ty = Syy - b * (Sy + (uint32_t)s);
+  const int U = (int)(Sxy - b * Sx - a * (uint32_t)s);
+  const float fr = small_int_to_float(r), fs = small_int_to_float(s);
+  const float fTx = __uint2float_rn(Tx), fTy = __uint2float_rn(Ty);
+  tt = fTx * fTy;
+  const float vx = fmaf(fn, fTx, -fr * fr);
+  const float vy = fmaf(fn, fTy, -fs * fs);
+  const float num = fmaf(fn, __int2float_rn(U), -fr * fs);
+  const float p = vx * vy;
+  const float cv = fminf(fmaxf(num * rsqrtf(p), -1.0f), 1.0f);
+  return p == 0.0f ? __int_as_float(0x7fc00000) : cv;
+}
+
+// Certificate: with every value of the window <= Mv, the second moment is
+// <= Mv * S; Mv * S < 2^32 for both channels makes Sxx and Syy exact.
+__device__ __forceinline__ bool certified(uint32_t Mx, uint32_t Sx, uint32_t My, uint32_t Sy) {
+  return (__umulhi(Mx, Sx) == 0u) && (__umulhi(My, Sy) == 0u);
+}
+
+// |U| <= sqrt(T_x T_y) < 2^31 when T_x T_y < 2^62 (float product, margin kept).
+constexpr float TT_LIMIT = 4.0e18f;
+
 // Process one work item.  Returns false if a bounded wait gave up (the
 // caller must then exit; in-flight copies have been drained).
 template <int M, int KW, bool TMA>
@@ -135,12 +171,11 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   const uint32_t NR = (uint32_t)rg.NR;
   const int PF = rg.PF;
 
-  auto issue = [&](int i) {
-    const uint32_t s = (seq + (uint32_t)i) % NR;
+  auto issue = [&](uint32_t s, int row) {
     if (!TMA) {
-      ldg_row_u16<G::RW>(rg.rx + (size_t)s * G::RWS, (const uint16_t*)sc.gx, sc.in_pitch, t0 + i, xs, sc.H, sc.W,
+      ldg_row_u16<G::RW>(rg.rx + (size_t)s * G::RWS, (const uint16_t*)sc.gx, sc.in_pitch, row, xs, sc.H, sc.W,
                          lane);
-      ldg_row_u16<G::RW>(rg.ry + (size_t)s * G::RWS, (const uint16_t*)sc.gy, sc.in_pitch, t0 + i, xs, sc.H, sc.W,
+      ldg_row_u16<G::RW>(rg.ry + (size_t)s * G::RWS, (const uint16_t*)sc.gy, sc.in_pitch, row, xs, sc.H, sc.W,
                          lane);
       return;
     }
@@ -148,29 +183,36 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     mbar_arrive_expect_tx(b, 2u * G::RW * 2u);
 #pragma unroll
     for (int q = 0; q < G::NMAIN; q++) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, t0 + i, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, t0 + i, b);
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, row, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, row, b);
     }
     if (G::TAIL > 0) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, t0 + i, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, t0 + i, b);
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, row, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, row, b);
     }
   };
-  if (TMA) {
-    if (lane == 0) {
-      fence_proxy_async_smem();
-      const int npre = min(PF, nrows);
-      for (int i = 0; i < npre; i++) issue(i);
-    }
-  } else {
+
+  // Ring bookkeeping without divisions in the row loop: slot of the entering
+  // row, its mbarrier phase, the leaving row's slot and the prefetch slot.
+  uint32_t s = seq % NR;
+  uint32_t lap = (seq / NR) & 1u;
+  uint32_t sl = (s + NR - (uint32_t)sc.kh % NR) % NR;
+  uint32_t sp = (s + (uint32_t)PF) % NR;
+  {
     const int npre = min(PF, nrows);
-    for (int i = 0; i < npre; i++) issue(i);
+    if (!TMA || lane == 0) {
+      if (TMA) fence_proxy_async_smem();
+      uint32_t si = s;
+      for (int i = 0; i < npre; i++) {
+        issue(si, t0 + i);
+        si = (si + 1 == NR) ? 0u : si + 1;
+      }
+    }
   }
 
-  // Lane geometry: centre columns [cl, cl + M); interior if its whole block
-  // of columns lies inside the grid.
   const int cl = cstrip + M * lane;
-  const bool col_interior = (cl - G::W1 >= 0) && (cl + M - 1 + G::W2 <= sc.W - 1);
+  const bool lane_border = (cl - G::W1 < 0) || (cl + M - 1 + G::W2 > sc.W - 1);
+  const bool fast_cols = sc.sx == 1 && sc.sums == nullptr && sc.vec_store;
   const uint32_t n_int = (uint32_t)(sc.kh * KW);
   const float fn_int = (float)n_int;
 
@@ -180,32 +222,29 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
 #pragma unroll
     for (int k = 0; k < 5; k++) V[c][k] = 0u;
   uint32_t mx2 = 0u, my2 = 0u;
+  int until_out = sc.kh - 1;  // rows until the next output row is complete
+  int jr = j0;
 
   for (int i = 0; i < nrows; i++) {
     __syncwarp();
-    if (TMA) {
-      if (lane == 0 && i + PF < nrows) {
-        fence_proxy_async_smem();
-        issue(i + PF);
-      }
-    } else if (i + PF < nrows) {
-      issue(i + PF);
+    if (i + PF < nrows && (!TMA || lane == 0)) {
+      if (TMA) fence_proxy_async_smem();
+      issue(sp, t0 + i + PF);
     }
-    const uint32_t q = seq + (uint32_t)i;
-    const uint32_t s = q % NR;
+    sp = (sp + 1 == NR) ? 0u : sp + 1;
     if (!TMA) {
       __syncwarp();
-    } else if (!mbar_wait_bounded(rg.bar + s, (q / NR) & 1u, status)) {
+    } else if (!mbar_wait_bounded(rg.bar + s, lap, status)) {
       // drain every copy still in flight into this CTA's ring, then give up
-      const int last = min(i + PF, nrows);
-      for (int k = i + 1; k < last; k++) {
-        const uint32_t qk = seq + (uint32_t)k;
-        mbar_wait_bounded(rg.bar + qk % NR, (qk / NR) & 1u, status);
+      uint32_t sk = s, lk = lap;
+      for (int k = i + 1; k <= min(i + PF, nrows - 1); k++) {
+        sk = (sk + 1 == NR) ? 0u : sk + 1;
+        if (sk == 0u) lk ^= 1u;
+        mbar_wait_bounded(rg.bar + sk, lk, status);
       }
       return false;
     }
     const bool has_leave = i >= sc.kh;
-    const uint32_t sl = (q + NR - (uint32_t)sc.kh % NR) % NR;
 
     uint32_t we[G::NWORD], wl[G::NWORD], ye[G::NWORD], yl[G::NWORD];
     {
@@ -234,9 +273,9 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       }
     }
 #pragma unroll
-    for (int w = 0; w < G::NWORD; w++) {
-      mx2 = __vmaxu2(mx2, we[w]);
-      my2 = __vmaxu2(my2, ye[w]);
+    for (int w = 0; w + 1 < G::NWORD; w += 2) {
+      mx2 = __vimax3_u16x2(mx2, we[w], we[w + 1]);
+      my2 = __vimax3_u16x2(my2, ye[w], ye[w + 1]);
     }
 
     // Row pass on the entering-minus-leaving differences, then the running
@@ -265,70 +304,95 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       }
     }
 
+    const uint32_t qrow = seq + (uint32_t)i;  // ring sequence number of this entering row
+    s = (s + 1 == NR) ? 0u : s + 1;
+    if (s == 0u) lap ^= 1u;
+    sl = (sl + 1 == NR) ? 0u : sl + 1;
+
     // Step 4 for the output row whose window is now complete.
-    const int rc = t0 + i - sc.h2;
-    if (i >= sc.kh - 1 && (rc % sc.sy) == 0) {
-      const int jr = rc / sc.sy;
-      const int cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
-      const bool interior = col_interior && (cnt_r == sc.kh);
+    if (until_out == 0) {
+      until_out = sc.sy;
+      const int rc = jr * sc.sy;
       const uint32_t Mx = max(mx2 & 0xFFFFu, mx2 >> 16), My = max(my2 & 0xFFFFu, my2 >> 16);
-      float res[M];
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-        const uint32_t Sx = V[c][0], Sy = V[c][1], Sxx = V[c][2], Syy = V[c][3], Sxy = V[c][4];
-        uint32_t n, a, b;
-        float fn;
-        if (interior) {
-          n = n_int;
-          fn = fn_int;
-          a = __umulhi(Sx, sc.inv_n);
-          b = __umulhi(Sy, sc.inv_n);
-        } else {
-          const int cc = cl + c;
-          const int cnt_c = min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1;
-          n = (uint32_t)(cnt_r * max(cnt_c, 1));
-          fn = (float)n;
-          const float rn = 1.0f / fn;
-          a = (uint32_t)((float)Sx * rn);
-          b = (uint32_t)((float)Sy * rn);
-        }
-        const int r = (int)(Sx - n * a), s2 = (int)(Sy - n * b);
-        const uint32_t Tx = Sxx - a * (Sx + (uint32_t)r);
-        const uint32_t Ty = Syy - b * (Sy + (uint32_t)s2);
-        const int U = (int)(Sxy - b * Sx - a * (uint32_t)s2);
-        const float fTx = (float)Tx, fTy = (float)Ty;
-        const float fr = (float)r, fs = (float)s2;
-        const float vx = fmaf(fn, fTx, -fr * fr);
-        const float vy = fmaf(fn, fTy, -fs * fs);
-        const float num = fmaf(fn, (float)U, -fr * fs);
-        float cv = num * rsqrtf(vx * vy);
-        cv = fminf(fmaxf(cv, -1.0f), 1.0f);
-        if (vx == 0.0f || vy == 0.0f) cv = __int_as_float(0x7fc00000);
-        const bool cert = (__umulhi(Mx, Sx) == 0u) && (__umulhi(My, Sy) == 0u) && (fTx * fTy < 4.0e18f);
-        const int cc = cl + c;
-        long long* s5 = nullptr;
-        if (sc.sums && cc < sc.W && (cc % sc.sx) == 0)
-          s5 = sc.sums + 5ll * ((long long)jr * sc.OW + cc / sc.sx);
-        if (!cert) {
-          cv = exact_window_u16<M, KW>(rg, q, sc.kh, lane, c, (int)n, s5);
-          atomicAdd(status + ST_FALLBACK, 1u);
-        } else if (s5) {
-          s5[0] = Sx; s5[1] = Sy; s5[2] = Sxx; s5[3] = Syy; s5[4] = Sxy;
-        }
-        res[c] = cv;
-      }
+      const bool row_interior = (rc - sc.h1 >= 0) && (rc + sc.h2 <= sc.H - 1);
       float* orow = sc.out + (long long)jr * sc.out_pitch;
-      if (sc.vec_store && cl + M <= sc.W) {
+      // one certificate for the whole lane row: its largest sums
+      uint32_t mSx = V[0][0], mSy = V[0][1];
 #pragma unroll
-        for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
-      } else {
+      for (int c = 1; c < M; c++) {
+        mSx = max(mSx, V[c][0]);
+        mSy = max(mSy, V[c][1]);
+      }
+      const bool row_cert = certified(Mx, mSx, My, mSy);
+      bool fast = fast_cols && row_interior && __all_sync(0xffffffffu, row_cert);
+      if (fast) {
+        float res[M];
+        float ttmax = 0.0f;
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          uint32_t n = n_int, inv = sc.inv_n;
+          float fn = fn_int;
+          if (lane_border) {
+            // clipped window columns: n and the reciprocal for the mean estimate
+            const int cc = cl + c;
+            const int cnt_c = max(min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1, 1);
+            n = (uint32_t)(sc.kh * cnt_c);
+            fn = (float)n;
+            inv = __float2uint_rz(4294967296.0f * __frcp_rn(fn));
+          }
+          float tt;
+          res[c] = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n, fn, __umulhi(V[c][0], inv),
+                               __umulhi(V[c][1], inv), tt);
+          ttmax = fmaxf(ttmax, tt);
+        }
+        // a cross term beyond int32 range (extremely wide, bright windows)
+        // sends the whole row through the per-window path below
+        fast = __all_sync(0xffffffffu, ttmax < TT_LIMIT);
+        if (fast) {
+          if (cl + M <= sc.W) {
+#pragma unroll
+            for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < M; c++)
+              if (cl + c < sc.W) orow[cl + c] = res[c];
+          }
+        }
+      }
+      if (!fast) {
+        // border rows or lanes, strided columns, debug sums, or a row whose
+        // certificate needs the per-window test: per-output n and checks
+        const int cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
 #pragma unroll
         for (int c = 0; c < M; c++) {
           const int cc = cl + c;
-          if (cc < sc.W && (cc % sc.sx) == 0) orow[cc / sc.sx] = res[c];
+          if (cc < sc.W && (sc.sx == 1 || (cc % sc.sx) == 0)) {
+            const int cnt_c = min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1;
+            const uint32_t n = (uint32_t)(cnt_r * cnt_c);
+            const float fn = (float)n;
+            const float rn = 1.0f / fn;
+            const uint32_t a = (uint32_t)((float)V[c][0] * rn), b = (uint32_t)((float)V[c][1] * rn);
+            const int jc = sc.sx == 1 ? cc : cc / sc.sx;
+            long long* s5 = sc.sums ? sc.sums + 5ll * ((long long)jr * sc.OW + jc) : nullptr;
+            float cv = 0.0f, tt = TT_LIMIT;
+            if (certified(Mx, V[c][0], My, V[c][1]))
+              cv = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n, fn, a, b, tt);
+            if (tt < TT_LIMIT) {
+              if (s5) {
+                s5[0] = V[c][0]; s5[1] = V[c][1]; s5[2] = V[c][2]; s5[3] = V[c][3]; s5[4] = V[c][4];
+              }
+            } else {
+              // rare: sums that may not be exact in 32 bits, recomputed exactly
+              cv = exact_window_u16<M, KW>(rg, qrow, sc.kh, lane, c, (int)n, s5);
+              atomicAdd(status + ST_FALLBACK, 1u);
+            }
+            orow[jc] = cv;
+          }
         }
       }
+      jr++;
     }
+    until_out--;
   }
   seq += (uint32_t)nrows;
   return true;

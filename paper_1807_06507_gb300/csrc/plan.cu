@@ -147,7 +147,7 @@ static swcorr_status plan_2d_u16(swcorr_plan_s* p) {
   sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
   const uint64_t n = (uint64_t)kh * (uint64_t)kw;
   sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
-  const int PF = 8;
+  const int PF = 4;
   const int NR = kh + 1 + PF;
   p->k2.NR = NR;
   p->k2.PF = PF;
@@ -155,7 +155,7 @@ static swcorr_status plan_2d_u16(swcorr_plan_s* p) {
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, p->smem);
   // one wave of work items over the resident warps
-  const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / (p->smem + 1024))));
+  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
   const int total = p->dev.sms * per_sm;
   int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
   TJ = std::max(TJ, std::max(16, 4 * kh / std::max(1, sc.sy)));
