@@ -156,6 +156,32 @@ swcorr_status swcorr_plan_status(swcorr_plan p);
  * certified below 2^32) since the last call; reading resets it.  -1 on error. */
 int64_t swcorr_plan_fallbacks(swcorr_plan p);
 
+/* No-allocation 2-D uint16 run, for callers that cannot allocate device
+ * memory: code whose device memory is owned by its own pool allocator under a
+ * fixed budget (e.g. a framework that reserved the GPU's memory up front), and
+ * latency-critical loops that must not call cudaMalloc/cudaFree because those
+ * calls can synchronise the whole device.  The paper has no counterpart: this
+ * is a deployment variant of swcorr_run for a 2-D uint16 plan with stride 1,
+ * computing the same results with the same kernel, but without a plan.
+ *   rows, cols : grid size; kh, kw: window (kw odd, 1..31).
+ *   x, y       : device uint16 grids; in_pitch elements between rows (<= 0
+ *                means cols).  c: device float32 output, out_pitch elements
+ *                between rows (<= 0 means cols).  stream: cudaStream_t.
+ * The kernel's scratch (its status words) lives in a 256-byte file-scope
+ * __device__ array of the library instead of a cudaMalloc'd block; every GPU
+ * that loads the library holds that array until the process exits.  The
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine); it rejects sizes beyond its limits (rows/cols >= 2^31 - 1024, or
+ * a kernel scratch larger than the array) with SWCORR_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array and clears its status words before launching, so calls
+ * whose work overlaps on the GPU (different streams, no ordering between
+ * them) race on it.  Asynchronous: returns after queuing. */
+swcorr_status swcorr_run2d_u16_noalloc(int64_t rows, int64_t cols, int32_t kh, int32_t kw, const void* x,
+                                       const void* y, int64_t in_pitch, float* c, int64_t out_pitch,
+                                       void* stream);
+
 /* Number of output windows the plan computes per run. */
 int64_t swcorr_plan_outputs(swcorr_plan p);
 

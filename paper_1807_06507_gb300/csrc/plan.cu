@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/swcorr.h"
+#include "hostapi.h"
 #include "launch.h"
 
 using namespace swc;
@@ -19,6 +20,10 @@ using namespace swc;
 namespace {
 
 thread_local std::string g_last_error;
+
+}  // namespace
+
+namespace swc {
 
 swcorr_status fail(swcorr_status st, const char* fmt, ...) {
   char buf[512];
@@ -33,6 +38,10 @@ swcorr_status fail(swcorr_status st, const char* fmt, ...) {
 swcorr_status cuda_fail(cudaError_t e, const char* what) {
   return fail(SWCORR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace swc
+
+namespace {
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda
 // link dependency).
@@ -53,6 +62,10 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+}  // namespace
+
+namespace swc {
+
 swcorr_status encode_2d(CUtensorMap* m, CUtensorMapDataType dt, int elem_bytes, const void* base, int64_t W,
                         int64_t H, int64_t pitch_elems, int box_w) {
   EncodeTiledFn fn = encode_fn();
@@ -68,13 +81,6 @@ swcorr_status encode_2d(CUtensorMap* m, CUtensorMapDataType dt, int elem_bytes, 
   return SWCORR_OK;
 }
 
-struct DeviceInfo {
-  int dev = -1;
-  int sms = 0;
-  int smem_optin = 0;
-  int cc_major = 0, cc_minor = 0;
-};
-
 swcorr_status device_info(DeviceInfo* d) {
   cudaError_t e = cudaGetDevice(&d->dev);
   if (e != cudaSuccess) return fail(SWCORR_ERR_NO_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
@@ -88,7 +94,78 @@ swcorr_status device_info(DeviceInfo* d) {
   return SWCORR_OK;
 }
 
-}  // namespace
+// Geometry, launch shape and per-launch constants of the 2-D uint16 kernel.
+swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, int sy, int sx, Geo2DInfo* g2,
+                           K2DParams* k2, size_t* smem_out, int* grid_out) {
+  if (!k2d_u16_geometry(kw, g2))
+    return fail(SWCORR_ERR_UNSUPPORTED, "2-D uint16: window width %d has no kernel instance (1..31 odd)", kw);
+  const Geo2DInfo& g = *g2;
+  Scene2D& sc = k2->sc;
+  sc.H = H;
+  sc.W = W;
+  sc.kh = kh;
+  sc.h1 = (kh - 1) / 2;
+  sc.h2 = kh / 2;
+  sc.kw = kw;
+  sc.sy = sy;
+  sc.sx = sx;
+  sc.OH = (H + sy - 1) / sy;
+  sc.OW = (W + sx - 1) / sx;
+  sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
+  const uint64_t n = (uint64_t)kh * (uint64_t)kw;
+  sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
+  const int PF = 4;
+  const int NR = kh + 1 + PF;
+  k2->NR = NR;
+  k2->PF = PF;
+  const size_t smem = (size_t)NR * g.RWS * 2 * 2 + (size_t)NR * 8;
+  if (smem > (size_t)dev.smem_optin)
+    return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, smem);
+  // one wave of work items over the resident warps
+  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (smem + 1024))));
+  const int total = dev.sms * per_sm;
+  int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
+  TJ = std::max(TJ, std::max(16, 4 * kh / std::max(1, sc.sy)));
+  TJ = std::min(TJ, sc.OH);
+  sc.TJ = TJ;
+  sc.n_rb = (sc.OH + TJ - 1) / TJ;
+  k2->n_items = sc.n_rb * sc.n_strips;
+  *grid_out = std::min(k2->n_items, total);
+  *smem_out = smem;
+  return SWCORR_OK;
+}
+
+// Pointers, pitches and (when the layout allows TMA) tensor maps of one 2-D
+// uint16 run; sets *use_tma.
+swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, const void* y, int64_t ip, float* c,
+                          int64_t op, int64_t* sums, bool encode_maps, bool* use_tma) {
+  const Scene2D& sc0 = k2->sc;
+  const int64_t W = sc0.W, H = sc0.H;
+  const bool base_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  // TMA needs 16-byte aligned bases and row pitches; anything else takes the
+  // plain-load row loader (same kernel, same results).
+  *use_tma = base_ok && (ip * 2) % 16 == 0;
+  if (*use_tma && encode_maps) {
+    swcorr_status s1 = encode_2d(&k2->tmx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, 256);
+    if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, 256);
+    if (s1 == SWCORR_OK && g2.TAIL > 0) {
+      s1 = encode_2d(&k2->tmx_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, g2.TAIL);
+      if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, g2.TAIL);
+    }
+    if (s1 != SWCORR_OK) return s1;
+  }
+  Scene2D& sc = k2->sc;
+  sc.gx = x;
+  sc.gy = y;
+  sc.in_pitch = ip;
+  sc.out = c;
+  sc.out_pitch = op;
+  sc.sums = reinterpret_cast<long long*>(sums);
+  sc.vec_store = (sc.sx == 1 && (reinterpret_cast<uintptr_t>(c) & 15) == 0 && (op % 4) == 0) ? 1 : 0;
+  return SWCORR_OK;
+}
+
+}  // namespace swc
 
 enum PlanKind { KIND_2D_U16 = 1, KIND_BATCHED = 10 };
 
@@ -128,43 +205,8 @@ static int64_t n_outputs(const swcorr_plan_s* p) {
 static size_t elem_size(swcorr_dtype dt) { return dt == SWCORR_U16 ? 2 : 4; }
 
 static swcorr_status plan_2d_u16(swcorr_plan_s* p) {
-  const int H = (int)p->shape[0], W = (int)p->shape[1];
-  const int kh = p->k[0], kw = p->k[1];
-  if (!k2d_u16_geometry(kw, &p->g2))
-    return fail(SWCORR_ERR_UNSUPPORTED, "2-D uint16: window width %d has no kernel instance (1..31 odd)", kw);
-  const Geo2DInfo& g = p->g2;
-  Scene2D& sc = p->k2.sc;
-  sc.H = H;
-  sc.W = W;
-  sc.kh = kh;
-  sc.h1 = (kh - 1) / 2;
-  sc.h2 = kh / 2;
-  sc.kw = kw;
-  sc.sy = p->stride[0];
-  sc.sx = p->stride[1];
-  sc.OH = (int)p->oshape[0];
-  sc.OW = (int)p->oshape[1];
-  sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
-  const uint64_t n = (uint64_t)kh * (uint64_t)kw;
-  sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
-  const int PF = 4;
-  const int NR = kh + 1 + PF;
-  p->k2.NR = NR;
-  p->k2.PF = PF;
-  p->smem = (size_t)NR * g.RWS * 2 * 2 + (size_t)NR * 8;
-  if (p->smem > (size_t)p->dev.smem_optin)
-    return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, p->smem);
-  // one wave of work items over the resident warps
-  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
-  const int total = p->dev.sms * per_sm;
-  int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
-  TJ = std::max(TJ, std::max(16, 4 * kh / std::max(1, sc.sy)));
-  TJ = std::min(TJ, sc.OH);
-  sc.TJ = TJ;
-  sc.n_rb = (sc.OH + TJ - 1) / TJ;
-  p->k2.n_items = sc.n_rb * sc.n_strips;
-  p->grid = std::min(p->k2.n_items, total);
-  return SWCORR_OK;
+  return setup_2d_u16(p->dev, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0], p->stride[1],
+                      &p->g2, &p->k2, &p->smem, &p->grid);
 }
 
 extern "C" {
@@ -247,44 +289,28 @@ int64_t swcorr_plan_outputs(swcorr_plan p) { return p ? n_outputs(p) : -1; }
 
 static swcorr_status run_2d_u16(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
                                 const int64_t* out_pitch, int64_t* sums, cudaStream_t st) {
-  const int64_t W = p->shape[1], H = p->shape[0];
+  const int64_t W = p->shape[1];
   const int64_t ip = in_pitch ? in_pitch[0] : W;
   if (in_pitch && in_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[1] must be 1");
   if (ip < W) return fail(SWCORR_ERR_INVALID_ARG, "in_pitch[0] = %lld < cols = %lld", (long long)ip, (long long)W);
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 1)
     return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
-  const bool base_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
-  // TMA needs 16-byte aligned bases and row pitches; anything else takes the
-  // plain-load row loader (same kernel, same results).
-  const bool tma = (ip * 2) % 16 == 0;
   const int64_t op = out_pitch ? out_pitch[0] : p->oshape[1];
   if (out_pitch && out_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "out_pitch[1] must be 1");
   if (op < p->oshape[1]) return fail(SWCORR_ERR_INVALID_ARG, "out_pitch[0] smaller than the output row");
-  const bool use_tma = tma && base_ok;
-  if (use_tma && (x != p->cached_x || y != p->cached_y || ip != p->cached_pitch)) {
-    swcorr_status s1 = encode_2d(&p->k2.tmx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, 256);
-    if (s1 == SWCORR_OK) s1 = encode_2d(&p->k2.tmy, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, 256);
-    if (s1 == SWCORR_OK && p->g2.TAIL > 0) {
-      s1 = encode_2d(&p->k2.tmx_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, p->g2.TAIL);
-      if (s1 == SWCORR_OK) s1 = encode_2d(&p->k2.tmy_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, p->g2.TAIL);
-    }
-    if (s1 != SWCORR_OK) {
-      p->cached_x = p->cached_y = nullptr;
-      return s1;
-    }
+  const bool cached = x == p->cached_x && y == p->cached_y && ip == p->cached_pitch;
+  bool use_tma = false;
+  swcorr_status s1 = bind_2d_u16(&p->k2, p->g2, x, y, ip, c, op, sums, !cached, &use_tma);
+  if (s1 != SWCORR_OK) {
+    p->cached_x = p->cached_y = nullptr;
+    return s1;
+  }
+  if (use_tma) {
     p->cached_x = x;
     p->cached_y = y;
     p->cached_pitch = ip;
   }
-  Scene2D& sc = p->k2.sc;
-  sc.gx = x;
-  sc.gy = y;
-  sc.in_pitch = ip;
-  sc.out = c;
-  sc.out_pitch = op;
-  sc.sums = reinterpret_cast<long long*>(sums);
-  sc.vec_store = (sc.sx == 1 && (reinterpret_cast<uintptr_t>(c) & 15) == 0 && (op % 4) == 0) ? 1 : 0;
-  cudaError_t e = k2d_u16_launch(sc.kw, p->k2, p->grid, p->smem, st, use_tma);
+  cudaError_t e = k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
   if (e != cudaSuccess) return cuda_fail(e, "2-D uint16 kernel launch");
   return SWCORR_OK;
 }

@@ -22,7 +22,7 @@ FLAG_EMIT_SUMS = 1
 
 EXPORTS = ("swcorr_plan_create", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_run_batched",
            "swcorr_plan_status", "swcorr_plan_fallbacks", "swcorr_plan_outputs", "swcorr_plan_destroy",
-           "swcorr_status_string", "swcorr_last_error", "swcorr_version")
+           "swcorr_status_string", "swcorr_last_error", "swcorr_version", "swcorr_run2d_u16_noalloc")
 
 
 class SwcorrError(RuntimeError):
@@ -69,6 +69,9 @@ def load(path: str | None = None):
         lib.swcorr_plan_outputs.restype = ctypes.c_int64
         lib.swcorr_plan_destroy.argtypes = [vp]
         lib.swcorr_plan_destroy.restype = None
+        lib.swcorr_run2d_u16_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp,
+                                                 vp, ctypes.c_int64, vp, ctypes.c_int64, vp]
+        lib.swcorr_run2d_u16_noalloc.restype = ctypes.c_int
         lib.swcorr_status_string.argtypes = [ctypes.c_int]
         lib.swcorr_status_string.restype = ctypes.c_char_p
         lib.swcorr_last_error.restype = ctypes.c_char_p
