@@ -121,6 +121,14 @@ __device__ __forceinline__ void ldg_row_u16(uint16_t* dst, const uint16_t* src, 
   }
 }
 
+// Clamp to [-1, 1] that keeps NaN (PTX max/min with .NaN).
+__device__ __forceinline__ float clamp1_nan(float v) {
+  float r;
+  asm("max.NaN.f32 %0, %1, -1.0;" : "=f"(r) : "f"(v));
+  asm("min.NaN.f32 %0, %0, 1.0;" : "+f"(r));
+  return r;
+}
+
 // Float of a small signed integer (|v| < 2^22) on the FMA/ALU pipes.
 __device__ __forceinline__ float small_int_to_float(int v) {
   return __int_as_float(0x4B400000 + v) - 12582912.0f;
@@ -141,9 +149,10 @@ __device__ __forceinline__ float pearson_u16(uint32_t Sx, uint32_t Sy, uint32_t 
   const float vx = fmaf(fn, fTx, -fr * fr);
   const float vy = fmaf(fn, fTy, -fs * fs);
   const float num = fmaf(fn, __int2float_rn(U), -fr * fs);
-  const float p = vx * vy;
-  const float cv = fminf(fmaxf(num * rsqrtf(p), -1.0f), 1.0f);
-  return p == 0.0f ? __int_as_float(0x7fc00000) : cv;
+  // A zero variance makes num exactly 0 (all values of one channel equal:
+  // n Sxy - Sx Sy = 0 in integers, and every term above is exact), so
+  // num * rsqrt(0) = 0 * inf = NaN, which the clamp keeps.
+  return clamp1_nan(num * rsqrtf(vx * vy));
 }
 
 // Certificate: with every value of the window <= Mv, the second moment is
@@ -211,10 +220,19 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   }
 
   const int cl = cstrip + M * lane;
-  const bool lane_border = (cl - G::W1 < 0) || (cl + M - 1 + G::W2 > sc.W - 1);
   const bool fast_cols = sc.sx == 1 && sc.sums == nullptr && sc.vec_store;
-  const uint32_t n_int = (uint32_t)(sc.kh * KW);
-  const float fn_int = (float)n_int;
+  // Window size n, its float and floor(2^32 / n) (mean estimate) for each of
+  // the lane's columns on interior rows; border columns have clipped counts.
+  uint32_t n_c[M], inv_c[M];
+  float fn_c[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    const int cc = cl + c;
+    const int cnt_c = max(min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1, 1);
+    n_c[c] = (uint32_t)(sc.kh * cnt_c);
+    fn_c[c] = (float)n_c[c];
+    inv_c[c] = n_c[c] == (uint32_t)(sc.kh * KW) ? sc.inv_n : __float2uint_rz(4294967296.0f * __frcp_rn(fn_c[c]));
+  }
 
   uint32_t V[M][5];
 #pragma unroll
@@ -316,33 +334,28 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       const uint32_t Mx = max(mx2 & 0xFFFFu, mx2 >> 16), My = max(my2 & 0xFFFFu, my2 >> 16);
       const bool row_interior = (rc - sc.h1 >= 0) && (rc + sc.h2 <= sc.H - 1);
       float* orow = sc.out + (long long)jr * sc.out_pitch;
-      // one certificate for the whole lane row: its largest sums
-      uint32_t mSx = V[0][0], mSy = V[0][1];
+      // one certificate for the whole lane row: n Mx^2 < 2^32 bounds every
+      // window's second moment; otherwise its largest sums are tested
+      const uint32_t n_max = (uint32_t)(sc.kh * KW);
+      bool row_cert = (__umulhi(Mx * Mx, n_max) == 0u) && (__umulhi(My * My, n_max) == 0u);
+      if (!row_cert) {
+        uint32_t mSx = V[0][0], mSy = V[0][1];
 #pragma unroll
-      for (int c = 1; c < M; c++) {
-        mSx = max(mSx, V[c][0]);
-        mSy = max(mSy, V[c][1]);
+        for (int c = 1; c < M; c++) {
+          mSx = max(mSx, V[c][0]);
+          mSy = max(mSy, V[c][1]);
+        }
+        row_cert = certified(Mx, mSx, My, mSy);
       }
-      const bool row_cert = certified(Mx, mSx, My, mSy);
       bool fast = fast_cols && row_interior && __all_sync(0xffffffffu, row_cert);
       if (fast) {
         float res[M];
         float ttmax = 0.0f;
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          uint32_t n = n_int, inv = sc.inv_n;
-          float fn = fn_int;
-          if (lane_border) {
-            // clipped window columns: n and the reciprocal for the mean estimate
-            const int cc = cl + c;
-            const int cnt_c = max(min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1, 1);
-            n = (uint32_t)(sc.kh * cnt_c);
-            fn = (float)n;
-            inv = __float2uint_rz(4294967296.0f * __frcp_rn(fn));
-          }
           float tt;
-          res[c] = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n, fn, __umulhi(V[c][0], inv),
-                               __umulhi(V[c][1], inv), tt);
+          res[c] = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n_c[c], fn_c[c],
+                               __umulhi(V[c][0], inv_c[c]), __umulhi(V[c][1], inv_c[c]), tt);
           ttmax = fmaxf(ttmax, tt);
         }
         // a cross term beyond int32 range (extremely wide, bright windows)
