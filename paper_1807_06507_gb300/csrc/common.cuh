@@ -88,6 +88,14 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Clamp to [-1, 1] that keeps NaN (PTX max/min with .NaN).
+__device__ __forceinline__ float clamp1_nan(float v) {
+  float r;
+  asm("max.NaN.f32 %0, %1, -1.0;" : "=f"(r) : "f"(v));
+  asm("min.NaN.f32 %0, %0, 1.0;" : "+f"(r));
+  return r;
+}
+
 __device__ __forceinline__ uint4 lds128(const void* p) {
   uint4 v;
   asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"

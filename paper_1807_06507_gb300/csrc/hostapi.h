@@ -27,7 +27,13 @@ swcorr_status device_info(DeviceInfo* d);
 swcorr_status encode_2d(CUtensorMap* m, CUtensorMapDataType dt, int elem_bytes, const void* base, int64_t W,
                         int64_t H, int64_t pitch_elems, int box_w);
 
-// Geometry, launch shape and per-launch constants of the 2-D uint16 kernel.
+// Geometry, launch shape and per-launch constants of the 2-D kernels.
+swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int kh, int kw, int sy, int sx,
+                       Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out);
+swcorr_status bind_2d(K2DParams* k2, const Geo2DInfo& g2, swcorr_dtype dt, const void* x, const void* y, int64_t ip,
+                      float* c, int64_t op, int64_t* sums, bool encode_maps, bool* use_tma);
+
+// The same for the 2-D uint16 kernel (used by the no-allocation entry point).
 swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, int sy, int sx, Geo2DInfo* g2,
                            K2DParams* k2, size_t* smem_out, int* grid_out);
 

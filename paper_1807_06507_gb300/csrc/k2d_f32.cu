@@ -1,0 +1,96 @@
+// k2d_f32.cu -- kernel entry points and instantiations of the fused 2-D
+// float32 correlation (one warp per CTA, persistent over work items).
+#include "k2d_f32.cuh"
+#include "launch.h"
+
+namespace swc {
+
+template <int M, int KW, bool TMA>
+__global__ void __launch_bounds__(32) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
+  using G = Geo2DF<M, KW>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Ring2DF rg;
+  rg.NR = p.NR;
+  rg.PF = p.PF;
+  rg.rx = reinterpret_cast<float*>(smem_raw);
+  rg.ry = rg.rx + (size_t)p.NR * G::RWS;
+  rg.bar = reinterpret_cast<uint64_t*>(rg.ry + (size_t)p.NR * G::RWS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
+    fence_mbar_init();
+    if (TMA) {
+      prefetch_tmap(&p.tmx);
+      prefetch_tmap(&p.tmy);
+      if (G::TAIL > 0) {
+        prefetch_tmap(&p.tmx_t);
+        prefetch_tmap(&p.tmy_t);
+      }
+    }
+  }
+  __syncwarp();
+  Scene2D sc = p.sc;
+  sc.tmx = &p.tmx;
+  sc.tmy = &p.tmy;
+  sc.tmx_t = &p.tmx_t;
+  sc.tmy_t = &p.tmy_t;
+  uint32_t seq = 0;
+  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    const int rb = item / sc.n_strips;
+    const int strip = item - rb * sc.n_strips;
+    if (!process_item_2d_f32<M, KW, TMA>(sc, strip, rb, rg, seq, p.status)) return;
+  }
+}
+
+template <int M, int KW, bool TMA>
+static cudaError_t launch_t(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k2d_f32_kernel<M, KW, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  k2d_f32_kernel<M, KW, TMA><<<grid, 32, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int M, int KW>
+static void geo(Geo2DInfo* g) {
+  using G = Geo2DF<M, KW>;
+  g->M = M;
+  g->KW = KW;
+  g->HALO = G::HALO;
+  g->RW = G::RW;
+  g->RWS = G::RWS;
+  g->TAIL = G::TAIL;
+}
+
+#define SWC_K2DF_CASES(X) X(8, 1) X(8, 3) X(8, 5) X(8, 7) X(8, 9) X(8, 11) X(8, 13) X(8, 15) X(8, 17) \
+  X(8, 19) X(8, 21) X(8, 23) X(8, 25) X(8, 27) X(8, 29) X(8, 31)
+
+bool k2d_f32_geometry(int kw, Geo2DInfo* g) {
+  switch (kw) {
+#define X(M, KW) \
+  case KW:       \
+    geo<M, KW>(g); \
+    return true;
+    SWC_K2DF_CASES(X)
+#undef X
+    default:
+      return false;
+  }
+}
+
+cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+  switch (kw) {
+#define X(M, KW) \
+  case KW:       \
+    return tma ? launch_t<M, KW, true>(p, grid, smem, st) : launch_t<M, KW, false>(p, grid, smem, st);
+    SWC_K2DF_CASES(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swc

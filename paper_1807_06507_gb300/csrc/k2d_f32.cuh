@@ -1,0 +1,344 @@
+// k2d_f32.cuh -- fused 2-D sliding-window correlation for float32 grids.
+//
+// Same structure as the uint16 kernel (Poyda & Zhizhin, Section 1, steps 1-4
+// fused; one warp per work item of 32*M centre columns x TJ output rows; a
+// TMA-fed row ring; row pass as in-lane prefix differences of the entering-
+// minus-leaving row, column pass as running sums), with one change of number
+// system: float32 sums of squares cannot be evaluated to 1e-5 of the Pearson
+// coefficient when a window's spread is small next to its offset, so each
+// lane maps its values to integers and sums exactly.
+//
+//  * Pass 1 streams the item's rows through the ring once and takes, per
+//    lane, the range [lo, hi] of x and of y over the lane's columns.
+//  * Each value becomes X = round((x - m) * 2^e), m the midpoint of [lo, hi]
+//    and 2^e the largest power of two with |x - m| * 2^e < 2^q, q = 22 when
+//    the window has at most 512 cells and 21 above (so that n^2 (2^q)^2, the
+//    bound of n Sxx - Sx^2, stays below 2^63).  x - m is one FADD (exact near m); one FFMA with the
+//    constant 1.5 * 2^23 rounds to the integer, one IADD extracts it.  The
+//    affine map is the same for every window of the lane, so it leaves
+//    Pearson's c unchanged; the rounding is the only error, at most
+//    2^-(q+1) * max|x - m| per value.
+//  * Cells outside the grid must add nothing.  Rows outside the grid (and the
+//    missing leaving row of the first kh-1 rows) are mapped to exactly 0 by a
+//    per-row switch of the scale to 0.  Columns outside the grid, which
+//    only a few border lanes see, enter as the constant G = X(0); since the
+//    sums are exact modular integers, step 4 subtracts their known count times
+//    G, G^2 and Gx*Gy exactly.
+//  * Pass 2 is the D-march with int32 first-moment and int64 second-moment
+//    sums, all exact; step 4 evaluates n Sxy - Sx Sy etc. exactly in int64 and
+//    rounds once to float32 per factor.  A zero variance gives NaN exactly.
+#pragma once
+
+#include "common.cuh"
+#include "kparams.h"
+
+namespace swc {
+
+template <int M, int KW>
+struct Geo2DF {
+  static constexpr int W1 = (KW - 1) / 2;
+  static constexpr int W2 = KW / 2;
+  static constexpr int HALO = (W1 <= 8 && W2 <= 8) ? 8 : 16;
+  static constexpr int RW = 32 * M + 2 * HALO;     // floats per row and channel
+  static constexpr int RWS = (RW + 31) / 32 * 32;  // ring row stride (128-byte rows)
+  static constexpr int NMAIN = RW / 256;
+  static constexpr int TAIL = RW - 256 * NMAIN;
+  static constexpr int OFF = HALO - W1;
+  static constexpr int CH0 = OFF / 4;              // first float4 of the lane
+  static constexpr int E0 = OFF % 4;
+  static constexpr int NCOL = M + KW - 1;
+  static constexpr int NCH = (E0 + NCOL + 3) / 4;  // float4 chunks per lane, row and channel
+  static_assert(TAIL % 4 == 0 && NMAIN >= 1, "row span cannot be split into TMA boxes");
+  static_assert(M % 4 == 0, "lane base must be 16-byte aligned");
+};
+
+struct Ring2DF {
+  float* rx;      // [NR][RWS]
+  float* ry;      // [NR][RWS]
+  uint64_t* bar;  // [NR]
+  int NR;
+  int PF;
+};
+
+// Fixed-point map of one channel of one lane (see the file header).
+struct Quant {
+  float m;  // reference (midpoint of the lane's range)
+  float s;  // 2^e; 0 maps every value to X = 0 (rows outside the grid)
+};
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
+
+__device__ __forceinline__ int quant(float x, const Quant& q) {
+  return __float_as_int(fmaf(x - q.m, q.s, kMagic)) - 0x4B400000;
+}
+
+__device__ __forceinline__ Quant make_quant(float lo, float hi, int qbits) {
+  if (!(lo <= hi)) lo = hi = 0.0f;  // a lane with no in-grid cell
+  Quant q;
+  q.m = lo + 0.5f * (hi - lo);
+  const float A = fmaxf(hi - q.m, q.m - lo);  // max |x - m|
+  int e = 0;
+  if (A > 0.0f) {
+    int ea;
+    frexpf(A, &ea);  // A < 2^ea
+    e = min(max(qbits - ea, -126), 126);
+  }
+  q.s = __int_as_float((127 + e) << 23);
+  return q;
+}
+
+template <int M, int KW, bool TMA>
+__device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip, int rb, const Ring2DF& rg,
+                                                    uint32_t& seq, uint32_t* status) {
+  using G = Geo2DF<M, KW>;
+  const int lane = threadIdx.x & 31;
+  const int j0 = rb * sc.TJ;
+  const int j1 = min(j0 + sc.TJ, sc.OH);
+  const int t0 = j0 * sc.sy - sc.h1;
+  const int nrows = (j1 - 1 - j0) * sc.sy + sc.kh;
+  const int cstrip = strip * 32 * M;
+  const int xs = cstrip - G::HALO;
+  const uint32_t NR = (uint32_t)rg.NR;
+  const int PF = rg.PF;
+
+  auto issue = [&](uint32_t s, int row) {
+    if (!TMA) {
+      const bool row_ok = row >= 0 && row < sc.H;
+      const float* gx = (const float*)sc.gx + (long long)(row_ok ? row : 0) * sc.in_pitch;
+      const float* gy = (const float*)sc.gy + (long long)(row_ok ? row : 0) * sc.in_pitch;
+      for (int e = lane; e < G::RW; e += 32) {
+        const int col = xs + e;
+        const bool ok = row_ok && col >= 0 && col < sc.W;
+        rg.rx[(size_t)s * G::RWS + e] = ok ? __ldg(gx + col) : 0.0f;
+        rg.ry[(size_t)s * G::RWS + e] = ok ? __ldg(gy + col) : 0.0f;
+      }
+      return;
+    }
+    uint64_t* b = rg.bar + s;
+    mbar_arrive_expect_tx(b, 2u * G::RW * 4u);
+#pragma unroll
+    for (int q = 0; q < G::NMAIN; q++) {
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, row, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, row, b);
+    }
+    if (G::TAIL > 0) {
+      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, row, b);
+      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, row, b);
+    }
+  };
+
+  // One streaming pass over the item's rows through the ring: issue ahead,
+  // wait, hand the slot to body(i, slot), keep the ring bookkeeping.
+  auto stream_rows = [&](auto&& body) -> bool {
+    uint32_t s = seq % NR, lap = (seq / NR) & 1u, sp = (s + (uint32_t)PF) % NR;
+    {
+      const int npre = min(PF, nrows);
+      if (!TMA || lane == 0) {
+        if (TMA) fence_proxy_async_smem();
+        uint32_t si = s;
+        for (int i = 0; i < npre; i++) {
+          issue(si, t0 + i);
+          si = (si + 1 == NR) ? 0u : si + 1;
+        }
+      }
+    }
+    for (int i = 0; i < nrows; i++) {
+      __syncwarp();
+      if (i + PF < nrows && (!TMA || lane == 0)) {
+        if (TMA) fence_proxy_async_smem();
+        issue(sp, t0 + i + PF);
+      }
+      sp = (sp + 1 == NR) ? 0u : sp + 1;
+      if (!TMA) {
+        __syncwarp();
+      } else if (!mbar_wait_bounded(rg.bar + s, lap, status)) {
+        uint32_t sk = s, lk = lap;
+        for (int k = i + 1; k <= min(i + PF, nrows - 1); k++) {
+          sk = (sk + 1 == NR) ? 0u : sk + 1;
+          if (sk == 0u) lk ^= 1u;
+          mbar_wait_bounded(rg.bar + sk, lk, status);
+        }
+        return false;
+      }
+      body(i, s);
+      s = (s + 1 == NR) ? 0u : s + 1;
+      if (s == 0u) lap ^= 1u;
+    }
+    seq += (uint32_t)nrows;
+    __syncwarp();
+    return true;
+  };
+
+  const int cl = cstrip + M * lane;
+  auto lane_ptr = [&](const float* ring, uint32_t slot) {
+    return ring + (size_t)slot * G::RWS + M * lane + G::CH0 * 4;
+  };
+
+  // ---- pass 1: value range of the lane's columns over the item's rows
+  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+  // in-grid columns of the lane: e in [e_lo, e_hi)
+  const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
+  if (!stream_rows([&](int i, uint32_t s) {
+        if (t0 + i < 0 || t0 + i >= sc.H) return;
+        const float* px = lane_ptr(rg.rx, s);
+        const float* py = lane_ptr(rg.ry, s);
+#pragma unroll
+        for (int h = 0; h < G::NCH; h++) {
+          const float4 a = *reinterpret_cast<const float4*>(px + 4 * h);
+          const float4 b = *reinterpret_cast<const float4*>(py + 4 * h);
+          const float va[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int e = 4 * h + u - G::E0;
+            if (e >= 0 && e < G::NCOL && e >= e_lo && e < e_hi) {
+              xlo = fminf(xlo, va[u]);
+              xhi = fmaxf(xhi, va[u]);
+              ylo = fminf(ylo, vb[u]);
+              yhi = fmaxf(yhi, vb[u]);
+            }
+          }
+        }
+      }))
+    return false;
+
+  const Quant qx = make_quant(xlo, xhi, sc.qbits), qy = make_quant(ylo, yhi, sc.qbits);
+  Quant qxe = qx, qye = qy, qxl = qx, qyl = qy;  // per-row maps (exact zero off the grid)
+  const bool lane_border = (cl - G::W1 < 0) || (cl + M - 1 + G::W2 > sc.W - 1);
+  const int Gx = quant(0.0f, qx), Gy = quant(0.0f, qy);  // value of an off-grid column
+
+  const bool fast_cols = sc.sx == 1 && sc.vec_store;
+  uint32_t n_c[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    const int cc = cl + c;
+    n_c[c] = (uint32_t)(sc.kh * max(min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1, 1));
+  }
+
+  // exact modular sums (wrapping unsigned arithmetic)
+  uint32_t V0[M], V1[M];
+  uint64_t V2[M], V3[M], V4[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    V0[c] = 0u; V1[c] = 0u; V2[c] = 0ull; V3[c] = 0ull; V4[c] = 0ull;
+  }
+  int until_out = sc.kh - 1;
+  int jr = j0;
+  const uint32_t seq0 = seq;
+
+  // ---- pass 2: the D-march on fixed-point values
+  const bool ok = stream_rows([&](int i, uint32_t s) {
+    const bool has_leave = i >= sc.kh;
+    const uint32_t sl = (uint32_t)(((int)s - sc.kh % (int)NR + (int)NR) % (int)NR);
+    const float* pxe = lane_ptr(rg.rx, s);
+    const float* pye = lane_ptr(rg.ry, s);
+    const float* pxl = lane_ptr(rg.rx, sl);
+    const float* pyl = lane_ptr(rg.ry, sl);
+    const int te = t0 + i, tl = te - sc.kh;
+    const bool e_ok = te >= 0 && te < sc.H;
+    const bool l_ok = has_leave && tl >= 0 && tl < sc.H;
+    qxe.s = e_ok ? qx.s : 0.0f;  // off-grid rows map to X = 0
+    qye.s = e_ok ? qy.s : 0.0f;
+    qxl.s = l_ok ? qx.s : 0.0f;  // so does the missing leaving row of warm-up
+    qyl.s = l_ok ? qy.s : 0.0f;
+    uint32_t P0 = 0u, P1 = 0u;
+    uint64_t P2 = 0ull, P3 = 0ull, P4 = 0ull;
+    uint32_t Ps0[M], Ps1[M];
+    uint64_t Ps2[M], Ps3[M], Ps4[M];
+#pragma unroll
+    for (int h = 0; h < G::NCH; h++) {
+      const float4 a = *reinterpret_cast<const float4*>(pxe + 4 * h);
+      const float4 b = *reinterpret_cast<const float4*>(pye + 4 * h);
+      float4 al = make_float4(0.f, 0.f, 0.f, 0.f), bl = al;
+      if (has_leave) {
+        al = *reinterpret_cast<const float4*>(pxl + 4 * h);
+        bl = *reinterpret_cast<const float4*>(pyl + 4 * h);
+      }
+      const float xa[4] = {a.x, a.y, a.z, a.w}, ya[4] = {b.x, b.y, b.z, b.w};
+      const float xla[4] = {al.x, al.y, al.z, al.w}, yla[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = 4 * h + u - G::E0;
+        if (e < 0 || e >= G::NCOL) continue;
+        const int Xe = quant(xa[u], qxe), Xl = quant(xla[u], qxl);
+        const int Ye = quant(ya[u], qye), Yl = quant(yla[u], qyl);
+        const int D = (int)((uint32_t)Xe - (uint32_t)Xl), S = (int)((uint32_t)Xe + (uint32_t)Xl);
+        const int Dy = (int)((uint32_t)Ye - (uint32_t)Yl), Sy = (int)((uint32_t)Ye + (uint32_t)Yl);
+        P0 += (uint32_t)D;
+        P1 += (uint32_t)Dy;
+        P2 += (uint64_t)((long long)D * S);
+        P3 += (uint64_t)((long long)Dy * Sy);
+        P4 += (uint64_t)((long long)D * Ye) + (uint64_t)((long long)Xl * Dy);
+        if (e >= KW - 1) {
+          const int c = e - (KW - 1);
+          V0[c] += P0 - (c >= 1 ? Ps0[c - 1] : 0u);
+          V1[c] += P1 - (c >= 1 ? Ps1[c - 1] : 0u);
+          V2[c] += P2 - (c >= 1 ? Ps2[c - 1] : 0ull);
+          V3[c] += P3 - (c >= 1 ? Ps3[c - 1] : 0ull);
+          V4[c] += P4 - (c >= 1 ? Ps4[c - 1] : 0ull);
+        }
+        if (e <= M - 2) {
+          Ps0[e] = P0; Ps1[e] = P1; Ps2[e] = P2; Ps3[e] = P3; Ps4[e] = P4;
+        }
+      }
+    }
+
+    if (until_out == 0) {
+      until_out = sc.sy;
+      const int rc = jr * sc.sy;
+      const int cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
+      float* orow = sc.out + (long long)jr * sc.out_pitch;
+      if (lane_border) {
+        // remove the off-grid columns' constant contribution (exact, modular)
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const uint32_t n_oob = (uint32_t)(cnt_r * (KW - (int)(n_c[c] / (uint32_t)sc.kh)));
+          V0[c] -= n_oob * (uint32_t)Gx;
+          V1[c] -= n_oob * (uint32_t)Gy;
+          V2[c] -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gx);
+          V3[c] -= (uint64_t)n_oob * (uint64_t)((long long)Gy * Gy);
+          V4[c] -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gy);
+        }
+      }
+      float res[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        const uint64_t n = cnt_r == sc.kh ? (uint64_t)n_c[c] : (uint64_t)(n_c[c] / sc.kh * cnt_r);
+        // exact in 64-bit modular arithmetic; the results are below 2^63
+        const uint64_t s0 = (uint64_t)(long long)(int)V0[c], s1 = (uint64_t)(long long)(int)V1[c];
+        const long long vx = (long long)(n * V2[c] - s0 * s0);
+        const long long vy = (long long)(n * V3[c] - s1 * s1);
+        const long long num = (long long)(n * V4[c] - s0 * s1);
+        // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
+        res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+      }
+      if (fast_cols && cl + M <= sc.W) {
+#pragma unroll
+        for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const int cc = cl + c;
+          if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) orow[sc.sx == 1 ? cc : cc / sc.sx] = res[c];
+        }
+      }
+      if (lane_border) {
+        // restore the running sums for the next rows
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const uint32_t n_oob = (uint32_t)(cnt_r * (KW - (int)(n_c[c] / (uint32_t)sc.kh)));
+          V0[c] += n_oob * (uint32_t)Gx;
+          V1[c] += n_oob * (uint32_t)Gy;
+          V2[c] += (uint64_t)n_oob * (uint64_t)((long long)Gx * Gx);
+          V3[c] += (uint64_t)n_oob * (uint64_t)((long long)Gy * Gy);
+          V4[c] += (uint64_t)n_oob * (uint64_t)((long long)Gx * Gy);
+        }
+      }
+      jr++;
+    }
+    until_out--;
+  });
+  (void)seq0;
+  return ok;
+}
+
+}  // namespace swc

@@ -121,14 +121,6 @@ __device__ __forceinline__ void ldg_row_u16(uint16_t* dst, const uint16_t* src, 
   }
 }
 
-// Clamp to [-1, 1] that keeps NaN (PTX max/min with .NaN).
-__device__ __forceinline__ float clamp1_nan(float v) {
-  float r;
-  asm("max.NaN.f32 %0, %1, -1.0;" : "=f"(r) : "f"(v));
-  asm("min.NaN.f32 %0, %0, 1.0;" : "+f"(r));
-  return r;
-}
-
 // Float of a small signed integer (|v| < 2^22) on the FMA/ALU pipes.
 __device__ __forceinline__ float small_int_to_float(int v) {
   return __int_as_float(0x4B400000 + v) - 12582912.0f;

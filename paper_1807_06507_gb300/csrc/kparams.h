@@ -38,7 +38,7 @@ struct Scene2D {
   float* out;
   long long out_pitch;     // elements between output rows
   long long* sums;         // optional 5 int64 per output (debug / bit-exact tests)
-  float qscale_unused;
+  int qbits;               // float32 path: fixed-point magnitude bits (|X| < 2^qbits)
 };
 
 struct K2DParams {

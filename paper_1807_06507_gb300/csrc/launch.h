@@ -16,4 +16,8 @@ struct Geo2DInfo {
 bool k2d_u16_geometry(int kw, Geo2DInfo* g);
 cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
 
+// 2-D float32: same interface.
+bool k2d_f32_geometry(int kw, Geo2DInfo* g);
+cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+
 }  // namespace swc

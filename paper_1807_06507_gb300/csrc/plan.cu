@@ -94,11 +94,13 @@ swcorr_status device_info(DeviceInfo* d) {
   return SWCORR_OK;
 }
 
-// Geometry, launch shape and per-launch constants of the 2-D uint16 kernel.
-swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, int sy, int sx, Geo2DInfo* g2,
-                           K2DParams* k2, size_t* smem_out, int* grid_out) {
-  if (!k2d_u16_geometry(kw, g2))
-    return fail(SWCORR_ERR_UNSUPPORTED, "2-D uint16: window width %d has no kernel instance (1..31 odd)", kw);
+// Geometry, launch shape and per-launch constants of the 2-D kernels.
+swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int kh, int kw, int sy, int sx,
+                       Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out) {
+  const bool f32 = dt == SWCORR_F32;
+  if (!(f32 ? k2d_f32_geometry(kw, g2) : k2d_u16_geometry(kw, g2)))
+    return fail(SWCORR_ERR_UNSUPPORTED, "2-D %s: window width %d has no kernel instance (1..31 odd)",
+                f32 ? "float32" : "uint16", kw);
   const Geo2DInfo& g = *g2;
   Scene2D& sc = k2->sc;
   sc.H = H;
@@ -114,11 +116,12 @@ swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, 
   sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
   const uint64_t n = (uint64_t)kh * (uint64_t)kw;
   sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
-  const int PF = 4;
+  sc.qbits = n <= 512 ? 22 : 21;  // n^2 * (2^qbits)^2 < 2^63
+  const int PF = f32 ? 3 : 4;
   const int NR = kh + 1 + PF;
   k2->NR = NR;
   k2->PF = PF;
-  const size_t smem = (size_t)NR * g.RWS * 2 * 2 + (size_t)NR * 8;
+  const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 2 + (size_t)NR * 8;
   if (smem > (size_t)dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, smem);
   // one wave of work items over the resident warps
@@ -135,22 +138,29 @@ swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, 
   return SWCORR_OK;
 }
 
+swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, int sy, int sx, Geo2DInfo* g2,
+                           K2DParams* k2, size_t* smem_out, int* grid_out) {
+  return setup_2d(dev, SWCORR_U16, H, W, kh, kw, sy, sx, g2, k2, smem_out, grid_out);
+}
+
 // Pointers, pitches and (when the layout allows TMA) tensor maps of one 2-D
 // uint16 run; sets *use_tma.
-swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, const void* y, int64_t ip, float* c,
-                          int64_t op, int64_t* sums, bool encode_maps, bool* use_tma) {
+swcorr_status bind_2d(K2DParams* k2, const Geo2DInfo& g2, swcorr_dtype dt, const void* x, const void* y, int64_t ip,
+                      float* c, int64_t op, int64_t* sums, bool encode_maps, bool* use_tma) {
   const Scene2D& sc0 = k2->sc;
   const int64_t W = sc0.W, H = sc0.H;
+  const int eb = dt == SWCORR_F32 ? 4 : 2;
+  const CUtensorMapDataType tdt = dt == SWCORR_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
   const bool base_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
   // TMA needs 16-byte aligned bases and row pitches; anything else takes the
   // plain-load row loader (same kernel, same results).
-  *use_tma = base_ok && (ip * 2) % 16 == 0;
+  *use_tma = base_ok && (ip * eb) % 16 == 0;
   if (*use_tma && encode_maps) {
-    swcorr_status s1 = encode_2d(&k2->tmx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, 256);
-    if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, 256);
+    swcorr_status s1 = encode_2d(&k2->tmx, tdt, eb, x, W, H, ip, 256);
+    if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy, tdt, eb, y, W, H, ip, 256);
     if (s1 == SWCORR_OK && g2.TAIL > 0) {
-      s1 = encode_2d(&k2->tmx_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, x, W, H, ip, g2.TAIL);
-      if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy_t, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, y, W, H, ip, g2.TAIL);
+      s1 = encode_2d(&k2->tmx_t, tdt, eb, x, W, H, ip, g2.TAIL);
+      if (s1 == SWCORR_OK) s1 = encode_2d(&k2->tmy_t, tdt, eb, y, W, H, ip, g2.TAIL);
     }
     if (s1 != SWCORR_OK) return s1;
   }
@@ -165,9 +175,14 @@ swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, con
   return SWCORR_OK;
 }
 
+swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, const void* y, int64_t ip, float* c,
+                          int64_t op, int64_t* sums, bool encode_maps, bool* use_tma) {
+  return bind_2d(k2, g2, SWCORR_U16, x, y, ip, c, op, sums, encode_maps, use_tma);
+}
+
 }  // namespace swc
 
-enum PlanKind { KIND_2D_U16 = 1, KIND_BATCHED = 10 };
+enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_BATCHED = 10 };
 
 struct swcorr_plan_s {
   int kind = 0;
@@ -204,9 +219,9 @@ static int64_t n_outputs(const swcorr_plan_s* p) {
 
 static size_t elem_size(swcorr_dtype dt) { return dt == SWCORR_U16 ? 2 : 4; }
 
-static swcorr_status plan_2d_u16(swcorr_plan_s* p) {
-  return setup_2d_u16(p->dev, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0], p->stride[1],
-                      &p->g2, &p->k2, &p->smem, &p->grid);
+static swcorr_status plan_2d(swcorr_plan_s* p) {
+  return setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0],
+                  p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid);
 }
 
 extern "C" {
@@ -258,9 +273,9 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
   }
   swcorr_status st = device_info(&tmp.dev);
   if (st != SWCORR_OK) return st;
-  if (ndim == 2 && dtype == SWCORR_U16) {
-    tmp.kind = KIND_2D_U16;
-    st = plan_2d_u16(&tmp);
+  if (ndim == 2) {
+    tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
+    st = plan_2d(&tmp);
   } else {
     st = fail(SWCORR_ERR_UNSUPPORTED, "ndim %d with dtype %s is not provided yet", ndim,
               dtype == SWCORR_U16 ? "u16" : "f32");
@@ -287,20 +302,20 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
 
 int64_t swcorr_plan_outputs(swcorr_plan p) { return p ? n_outputs(p) : -1; }
 
-static swcorr_status run_2d_u16(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
-                                const int64_t* out_pitch, int64_t* sums, cudaStream_t st) {
+static swcorr_status run_2d(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                            const int64_t* out_pitch, int64_t* sums, cudaStream_t st) {
   const int64_t W = p->shape[1];
   const int64_t ip = in_pitch ? in_pitch[0] : W;
   if (in_pitch && in_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[1] must be 1");
   if (ip < W) return fail(SWCORR_ERR_INVALID_ARG, "in_pitch[0] = %lld < cols = %lld", (long long)ip, (long long)W);
-  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 1)
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & (elem_size(p->dtype) - 1))
     return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
   const int64_t op = out_pitch ? out_pitch[0] : p->oshape[1];
   if (out_pitch && out_pitch[1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "out_pitch[1] must be 1");
   if (op < p->oshape[1]) return fail(SWCORR_ERR_INVALID_ARG, "out_pitch[0] smaller than the output row");
   const bool cached = x == p->cached_x && y == p->cached_y && ip == p->cached_pitch;
   bool use_tma = false;
-  swcorr_status s1 = bind_2d_u16(&p->k2, p->g2, x, y, ip, c, op, sums, !cached, &use_tma);
+  swcorr_status s1 = bind_2d(&p->k2, p->g2, p->dtype, x, y, ip, c, op, sums, !cached, &use_tma);
   if (s1 != SWCORR_OK) {
     p->cached_x = p->cached_y = nullptr;
     return s1;
@@ -310,8 +325,9 @@ static swcorr_status run_2d_u16(swcorr_plan_s* p, const void* x, const void* y, 
     p->cached_y = y;
     p->cached_pitch = ip;
   }
-  cudaError_t e = k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
-  if (e != cudaSuccess) return cuda_fail(e, "2-D uint16 kernel launch");
+  cudaError_t e = p->dtype == SWCORR_F32 ? k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma)
+                                         : k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
+  if (e != cudaSuccess) return cuda_fail(e, "2-D kernel launch");
   return SWCORR_OK;
 }
 
@@ -326,7 +342,8 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   if (!(p->flags & SWCORR_FLAG_EMIT_SUMS)) sums = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   switch (p->kind) {
-    case KIND_2D_U16: return run_2d_u16(p, x, y, in_pitch, c, out_pitch, sums, st);
+    case KIND_2D_U16:
+    case KIND_2D_F32: return run_2d(p, x, y, in_pitch, c, out_pitch, sums, st);
   }
   return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);
 }
