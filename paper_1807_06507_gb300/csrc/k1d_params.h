@@ -1,0 +1,29 @@
+// k1d_params.h -- parameters of the fused 1-D kernel (host and device).
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+namespace swc {
+
+struct K1DParams {
+  CUtensorMap tmx;  // 1-D maps: dims {N}, box {256}
+  CUtensorMap tmy;
+  long long N;       // series length
+  int k, h1, h2;     // window and its extents before/after the centre
+  int stride;
+  long long n_out;   // ceil(N / stride)
+  long long n_items; // chunks
+  int span;          // cells loaded per chunk, rounded up to whole boxes
+  int nbox;          // TMA boxes per channel per chunk
+  int q, r;          // k = q * (M1 * stride) + r
+  int nseg;          // segments of M1*stride cells in the span (<= 64)
+  int is_f32;
+  int qbits;         // float32 fixed-point magnitude bits
+  const void* gx;    // plain-load fallback (unaligned bases)
+  const void* gy;
+  float* out;
+  uint32_t* status;
+};
+
+}  // namespace swc

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "kparams.h"
+#include "k1d_params.h"
 
 namespace swc {
 
@@ -19,5 +20,9 @@ cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
 // 2-D float32: same interface.
 bool k2d_f32_geometry(int kw, Geo2DInfo* g);
 cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+
+// 1-D (uint16 or float32): outputs per lane per chunk, and the launch.
+int k1d_outputs_per_lane();
+cudaError_t k1d_launch(const K1DParams& p, int grid, size_t smem, cudaStream_t st);
 
 }  // namespace swc

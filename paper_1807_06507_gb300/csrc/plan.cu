@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -78,6 +79,20 @@ swcorr_status encode_2d(CUtensorMap* m, CUtensorMapDataType dt, int elem_bytes, 
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return SWCORR_OK;
+}
+
+swcorr_status encode_1d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, int64_t N) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[1] = {(cuuint64_t)N};
+  cuuint64_t strides[1] = {0};
+  cuuint32_t box[1] = {256u};
+  cuuint32_t estr[1] = {1u};
+  CUresult r = fn(m, dt, 1, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled (1-D) failed (CUresult %d)", (int)r);
   return SWCORR_OK;
 }
 
@@ -182,7 +197,7 @@ swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, con
 
 }  // namespace swc
 
-enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_BATCHED = 10 };
+enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_BATCHED = 10 };
 
 struct swcorr_plan_s {
   int kind = 0;
@@ -199,6 +214,8 @@ struct swcorr_plan_s {
   K2DParams k2{};
   int grid = 0;
   size_t smem = 0;
+  // 1-D launch
+  K1DParams k1{};
   // tensor-map cache
   const void* cached_x = nullptr;
   const void* cached_y = nullptr;
@@ -218,6 +235,74 @@ static int64_t n_outputs(const swcorr_plan_s* p) {
 }
 
 static size_t elem_size(swcorr_dtype dt) { return dt == SWCORR_U16 ? 2 : 4; }
+
+static swcorr_status plan_1d(swcorr_plan_s* p) {
+  K1DParams& k1 = p->k1;
+  const int64_t N = p->shape[0];
+  const int k = p->k[0], s = p->stride[0];
+  const int M1 = k1d_outputs_per_lane();
+  const int L = 32 * M1;
+  const int64_t seg = (int64_t)M1 * s;
+  const int64_t q = k / seg;
+  if (q > 31)
+    return fail(SWCORR_ERR_UNSUPPORTED, "1-D window %d longer than 32 * %d * stride", k, M1);
+  k1.N = N;
+  k1.k = k;
+  k1.h1 = (k - 1) / 2;
+  k1.h2 = k / 2;
+  k1.stride = s;
+  k1.n_out = (N + s - 1) / s;
+  k1.n_items = (k1.n_out + L - 1) / L;
+  k1.q = (int)q;
+  k1.r = (int)(k % seg);
+  k1.nseg = (int)std::min<int64_t>(64, 32 + q + 1);
+  k1.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
+  const int align = k1.is_f32 ? 4 : 8;
+  const int64_t need = align + (int64_t)(L - 1) * s + k + seg;  // span plus slack for the last segment
+  k1.nbox = (int)((need + 255) / 256);
+  k1.span = k1.nbox * 256;
+  // fixed point for float32: k^2 (2^qbits)^2 < 2^62
+  int qb = 22;
+  while (qb > 8 && 2.0 * std::log2((double)k) + 2.0 * qb >= 62.0) qb--;
+  k1.qbits = qb;
+  p->smem = (size_t)2 * k1.span * 4 + (size_t)L * 4 + 16;
+  if (p->smem > (size_t)p->dev.smem_optin)
+    return fail(SWCORR_ERR_UNSUPPORTED, "1-D window %d with stride %d needs %zu B of shared memory", k, s, p->smem);
+  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
+  p->grid = (int)std::min<int64_t>(k1.n_items, (int64_t)p->dev.sms * per_sm);
+  return SWCORR_OK;
+}
+
+static swcorr_status run_1d(swcorr_plan_s* p, const void* x, const void* y, float* c, cudaStream_t st) {
+  K1DParams& k1 = p->k1;
+  const size_t es = elem_size(p->dtype);
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & (es - 1))
+    return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
+  const bool tma = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  if (tma) {
+    if (x != p->cached_x || y != p->cached_y) {
+      const CUtensorMapDataType dt =
+          p->dtype == SWCORR_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+      swcorr_status s1 = encode_1d(&k1.tmx, dt, x, k1.N);
+      if (s1 == SWCORR_OK) s1 = encode_1d(&k1.tmy, dt, y, k1.N);
+      if (s1 != SWCORR_OK) {
+        p->cached_x = p->cached_y = nullptr;
+        return s1;
+      }
+      p->cached_x = x;
+      p->cached_y = y;
+    }
+    k1.gx = k1.gy = nullptr;
+  } else {
+    k1.gx = x;
+    k1.gy = y;
+  }
+  k1.out = c;
+  k1.status = p->d_status;
+  cudaError_t e = k1d_launch(k1, p->grid, p->smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "1-D kernel launch");
+  return SWCORR_OK;
+}
 
 static swcorr_status plan_2d(swcorr_plan_s* p) {
   return setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0],
@@ -276,6 +361,9 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
   if (ndim == 2) {
     tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
     st = plan_2d(&tmp);
+  } else if (ndim == 1) {
+    tmp.kind = KIND_1D;
+    st = plan_1d(&tmp);
   } else {
     st = fail(SWCORR_ERR_UNSUPPORTED, "ndim %d with dtype %s is not provided yet", ndim,
               dtype == SWCORR_U16 ? "u16" : "f32");
@@ -344,6 +432,11 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   switch (p->kind) {
     case KIND_2D_U16:
     case KIND_2D_F32: return run_2d(p, x, y, in_pitch, c, out_pitch, sums, st);
+    case KIND_1D:
+      if (sums) return fail(SWCORR_ERR_UNSUPPORTED, "1-D plans do not emit sums");
+      if ((in_pitch && in_pitch[0] != 1) || (out_pitch && out_pitch[0] != 1))
+        return fail(SWCORR_ERR_UNSUPPORTED, "1-D series must be contiguous");
+      return run_1d(p, x, y, c, st);
   }
   return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);
 }
