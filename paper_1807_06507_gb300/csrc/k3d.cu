@@ -1,0 +1,60 @@
+// k3d.cu -- instantiations and launch of the fused 3-D correlation kernel.
+#include "k3d.cuh"
+#include "launch.h"
+
+namespace swc {
+
+constexpr int kTY3 = 8, kTX3 = 128;
+
+template <int K>
+static cudaError_t launch_k(const K3DParams& p, int grid, size_t smem, cudaStream_t st) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k3d_kernel<kTY3, kTX3, K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  k3d_kernel<kTY3, kTX3, K, K><<<grid, K3_THREADS, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int K>
+static void geo(Geo3DInfo* g) {
+  using G = Geo3D<kTY3, kTX3, K, K>;
+  g->TY = kTY3;
+  g->TX = kTX3;
+  g->TYI = G::TYI;
+  g->BXW = G::BXW;
+  g->XH = G::XH;
+  g->VSP = G::VSP;
+}
+
+#define SWC_K3D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15)
+
+bool k3d_geometry(int k, Geo3DInfo* g) {
+  switch (k) {
+#define X(K) \
+  case K:    \
+    geo<K>(g); \
+    return true;
+    SWC_K3D_CASES(X)
+#undef X
+    default:
+      return false;
+  }
+}
+
+cudaError_t k3d_launch(int k, const K3DParams& p, int grid, size_t smem, cudaStream_t st) {
+  switch (k) {
+#define X(K) \
+  case K:    \
+    return launch_k<K>(p, grid, smem, st);
+    SWC_K3D_CASES(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swc

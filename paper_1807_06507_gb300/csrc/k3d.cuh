@@ -1,0 +1,370 @@
+// k3d.cuh -- fused 3-D sliding-window correlation (uint16 or float32).
+//
+// The n-dimensional generalisation of the optimized algorithm (Poyda &
+// Zhizhin, Section 1: one sliding-sum pass per dimension; parallel scheme of
+// Section 2 extended to the third dimension), fused into one kernel.
+//
+// A CTA of 128 threads owns a footprint of TY output rows x TX output
+// columns and marches along z over a block of TZ output planes:
+//  * Each z-step brings the entering plane (z + kz/2) and the leaving plane
+//    (z - (kz-1)/2 - 1) of the footprint's input rectangle into shared memory
+//    with 3-D TMA boxes (zero fill off the volume); the leaving plane comes
+//    back from L2, where it was read kz steps earlier.
+//  * Values become exact integers (uint16 as they are; float32 through one
+//    fixed-point map per work item, taken in a first pass over its planes).
+//    Off-volume cells map to 0.
+//  * Vertical pass: one thread per input column forms, for every row of the
+//    rectangle, the five entering-minus-leaving streams (x, y, x^2, y^2, xy
+//    differences), their running prefix down the column, and the window sums
+//    of ky rows as prefix differences (snapshots kept in registers); the
+//    results go to a structure-of-arrays buffer.
+//  * Horizontal pass: each lane takes 4 output columns of 2 output rows, sums
+//    kx columns of that buffer as prefix differences, and adds the result to
+//    its running 3-D sums (registers), which are therefore the sums over the
+//    kz x ky x kx window of the current output plane.
+//  * Step 4 (Eq. 2) exactly in int64 once the plane's window is complete.
+// All sums are modular integers (uint32 / uint64), hence exact.
+#pragma once
+
+#include "common.cuh"
+#include "kparams.h"
+
+namespace swc {
+
+struct K3DParams {
+  CUtensorMap tmx;  // 3-D maps: dims {W, H, Z}, box {BXW, TY + ky - 1, 1}
+  CUtensorMap tmy;
+  int Z, H, W;
+  int kz, hz1, hz2;
+  int sz, sy, sx;
+  int OZ, OY, OX;
+  int TZ;            // output planes per work item
+  int nzb, nyb, nxb;
+  int n_items;
+  int is_f32;
+  int qbits;
+  long long opz, opy;  // output pitches (elements) of a plane and of a row
+  float* out;
+  uint32_t* status;
+  int use_tma;         // 0: plain loads (pitches TMA cannot describe)
+  const void* gx;
+  const void* gy;
+  long long ipy, ipz;  // input pitches (elements) of a row and of a plane
+};
+
+constexpr int K3_THREADS = 128;
+
+template <int TY, int TX, int KY, int KX>
+struct Geo3D {
+  static constexpr int H1 = (KY - 1) / 2, H2 = KY / 2;
+  static constexpr int W1 = (KX - 1) / 2, W2 = KX / 2;
+  static constexpr int TYI = TY + KY - 1;          // input rows of the footprint
+  static constexpr int TXI = TX + KX - 1;          // input columns of the footprint
+  static constexpr int XH = (W1 + 7) / 8 * 8;      // aligned left halo loaded
+  static constexpr int BXW = ((XH + TX + W2) + 7) / 8 * 8;  // box width (elements)
+  static constexpr int COFF = XH - W1;             // column 0 of the footprint in the box
+  static constexpr int VSP = TXI + 4;              // padded row of the vertical-sum buffer
+  static_assert(BXW <= 256, "box too wide");
+};
+
+template <int TY, int TX, int KY, int KX>
+__global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__ K3DParams p) {
+  using G = Geo3D<TY, TX, KY, KX>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int esz = p.is_f32 ? 4 : 2;
+  const size_t plane_bytes = (size_t)G::TYI * G::BXW * esz;   // one channel of one plane
+  const size_t plane_stride = (plane_bytes + 127) / 128 * 128;  // TMA destinations are 128-byte aligned
+  const size_t slot_bytes = 2 * plane_stride;                   // x, then y
+  const int yoff = (int)(plane_stride / esz);                    // y channel, in elements
+  // slots: [0,1] entering, [2,3] leaving
+  unsigned char* slots = smem_raw;
+  uint32_t* VS = reinterpret_cast<uint32_t*>(smem_raw + 4 * slot_bytes);  // [8][TY][VSP]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(VS + 8 * TY * G::VSP);      // 4 mbarriers
+  __shared__ float red[4][K3_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) {
+    for (int b = 0; b < 4; b++) mbar_init(bar + b, 1);
+    fence_mbar_init();
+    if (p.use_tma) {
+      prefetch_tmap(&p.tmx);
+      prefetch_tmap(&p.tmy);
+    }
+  }
+  __syncthreads();
+  uint32_t phase_bits = 0;  // parity of each of the 4 barriers
+
+  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    int rem = item;
+    const int xb = rem % p.nxb; rem /= p.nxb;
+    const int yb = rem % p.nyb; rem /= p.nyb;
+    const int zbk = rem;
+    const int x0 = xb * TX, y0 = yb * TY;              // first centre column / row of the footprint
+    const int zc0 = zbk * p.TZ;                        // first centre plane
+    const int zc1 = min(zc0 + p.TZ, p.Z);
+    const int ze0 = zc0 - p.hz1;                       // first entering plane
+    const int nsteps = (zc1 - zc0) + p.kz - 1;
+    const int bx = x0 - G::XH, by = y0 - G::H1;        // box origin
+
+    auto issue = [&](int slot, int z) {  // thread 0 only
+      uint64_t* b = bar + slot;
+      unsigned char* d = slots + slot * slot_bytes;
+      mbar_arrive_expect_tx(b, (uint32_t)(2 * plane_bytes));
+      tma_load_3d(d, &p.tmx, bx, by, z, b);
+      tma_load_3d(d + plane_stride, &p.tmy, bx, by, z, b);
+    };
+    auto wait_slot = [&](int slot) -> bool {
+      if (!p.use_tma) return true;
+      const bool ok = mbar_wait_bounded(bar + slot, (phase_bits >> slot) & 1u, p.status);
+      phase_bits ^= (1u << slot);
+      return ok;
+    };
+    // plain-load variant of issue(): the whole CTA copies the box (zero fill
+    // off the volume); the caller synchronises before use
+    auto load_plain = [&](int slot, int z) {
+      unsigned char* d = slots + slot * slot_bytes;
+      const bool z_ok = z >= 0 && z < p.Z;
+      for (int e = tid; e < G::TYI * G::BXW; e += K3_THREADS) {
+        const int r = e / G::BXW, cidx = e - r * G::BXW;
+        const int gy = by + r, gxx = bx + cidx;
+        const bool ok = z_ok && gy >= 0 && gy < p.H && gxx >= 0 && gxx < p.W;
+        const long long g = (long long)z * p.ipz + (long long)gy * p.ipy + gxx;
+        if (esz == 4) {
+          reinterpret_cast<float*>(d)[e] = ok ? __ldg((const float*)p.gx + g) : 0.0f;
+          reinterpret_cast<float*>(d + plane_stride)[e] = ok ? __ldg((const float*)p.gy + g) : 0.0f;
+        } else {
+          reinterpret_cast<uint16_t*>(d)[e] = ok ? __ldg((const uint16_t*)p.gx + g) : (uint16_t)0;
+          reinterpret_cast<uint16_t*>(d + plane_stride)[e] = ok ? __ldg((const uint16_t*)p.gy + g) : (uint16_t)0;
+        }
+      }
+    };
+
+    // ---- float32: one fixed-point map for the item (pass over its planes)
+    float qmx = 0.f, qsx = 1.f, qmy = 0.f, qsy = 1.f;
+    if (p.is_f32) {
+      float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+      if (tid == 0 && p.use_tma) {
+        fence_proxy_async_smem();
+        issue(0, ze0);
+      }
+      for (int s = 0; s < nsteps; s++) {
+        if (!p.use_tma) {
+          load_plain(s & 1, ze0 + s);
+          __syncthreads();
+        } else if (tid == 0 && s + 1 < nsteps) {
+          fence_proxy_async_smem();
+          issue((s + 1) & 1, ze0 + s + 1);
+        }
+        if (!wait_slot(s & 1)) return;
+        const int z = ze0 + s;
+        if (z >= 0 && z < p.Z) {
+          const float* px = reinterpret_cast<const float*>(slots + (s & 1) * slot_bytes);
+          const float* py = px + yoff;
+          for (int e = tid; e < G::TYI * G::TXI; e += K3_THREADS) {
+            const int r = e / G::TXI, c = e - r * G::TXI;
+            const int gy = by + r, gxx = x0 - G::W1 + c;
+            if (gy >= 0 && gy < p.H && gxx >= 0 && gxx < p.W) {
+              const float a = px[r * G::BXW + G::COFF + c], b = py[r * G::BXW + G::COFF + c];
+              xlo = fminf(xlo, a); xhi = fmaxf(xhi, a); ylo = fminf(ylo, b); yhi = fmaxf(yhi, b);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // block reduction
+      for (int o = 16; o > 0; o >>= 1) {
+        xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, o));
+        xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, o));
+        ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
+        yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
+      }
+      if (lane == 0) {
+        red[0][warp] = xlo; red[1][warp] = xhi; red[2][warp] = ylo; red[3][warp] = yhi;
+      }
+      __syncthreads();
+      xlo = red[0][0]; xhi = red[1][0]; ylo = red[2][0]; yhi = red[3][0];
+      for (int w = 1; w < K3_THREADS / 32; w++) {
+        xlo = fminf(xlo, red[0][w]); xhi = fmaxf(xhi, red[1][w]);
+        ylo = fminf(ylo, red[2][w]); yhi = fmaxf(yhi, red[3][w]);
+      }
+      __syncthreads();
+      auto mk = [&](float lo, float hi, float& m, float& s) {
+        if (!(lo <= hi)) lo = hi = 0.0f;
+        m = lo + 0.5f * (hi - lo);
+        const float A = fmaxf(hi - m, m - lo);
+        int e = 0;
+        if (A > 0.0f) {
+          int ea;
+          frexpf(A, &ea);
+          e = min(max(p.qbits - ea, -126), 126);
+        }
+        s = __int_as_float((127 + e) << 23);
+      };
+      mk(xlo, xhi, qmx, qsx);
+      mk(ylo, yhi, qmy, qsy);
+    }
+
+    // ---- the z-march
+    uint32_t V0[2][4], V1[2][4];
+    uint64_t V2[2][4], V3[2][4], V4[2][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        V0[a][c] = V1[a][c] = 0u;
+        V2[a][c] = V3[a][c] = V4[a][c] = 0ull;
+      }
+    // entering plane of step s in slot s&1, leaving plane (step s >= kz) in
+    // slot 2 + (s&1); both are requested one step ahead
+    if (tid == 0 && p.use_tma) {
+      fence_proxy_async_smem();
+      issue(0, ze0);
+    }
+    for (int s = 0; s < nsteps; s++) {
+      const int ze = ze0 + s, zl = ze - p.kz;
+      const bool has_leave = s >= p.kz;
+      if (!p.use_tma) {
+        load_plain(s & 1, ze);
+        if (has_leave) load_plain(2 + (s & 1), zl);
+        __syncthreads();
+      } else if (tid == 0 && s + 1 < nsteps) {
+        fence_proxy_async_smem();
+        issue((s + 1) & 1, ze + 1);
+        if (s + 1 >= p.kz) issue(2 + ((s + 1) & 1), ze + 1 - p.kz);
+      }
+      if (!wait_slot(s & 1)) return;
+      if (has_leave && !wait_slot(2 + (s & 1))) return;
+      const bool ze_ok = ze >= 0 && ze < p.Z;
+      const bool zl_ok = has_leave && zl >= 0 && zl < p.Z;
+      const unsigned char* se = slots + (s & 1) * slot_bytes;
+      const unsigned char* sl = slots + (2 + (s & 1)) * slot_bytes;
+
+      // vertical pass: thread per input column
+      for (int c = tid; c < G::TXI; c += K3_THREADS) {
+        const int gxx = x0 - G::W1 + c;
+        const bool col_ok = gxx >= 0 && gxx < p.W;
+        const float fse_x = (col_ok && ze_ok) ? qsx : 0.f, fsl_x = (col_ok && zl_ok) ? qsx : 0.f;
+        const float fse_y = (col_ok && ze_ok) ? qsy : 0.f, fsl_y = (col_ok && zl_ok) ? qsy : 0.f;
+        const bool ue = col_ok && ze_ok, ul = col_ok && zl_ok;
+        uint32_t P0 = 0u, P1 = 0u;
+        uint64_t P2 = 0ull, P3 = 0ull, P4 = 0ull;
+        uint32_t S0[TY], S1[TY];
+        uint64_t S2[TY], S3[TY], S4[TY];
+#pragma unroll
+        for (int r = 0; r < G::TYI; r++) {
+          const int gy = by + r;
+          const bool row_ok = gy >= 0 && gy < p.H;
+          const int idx = r * G::BXW + G::COFF + c;
+          int Xe, Xl, Ye, Yl;
+          if (p.is_f32) {
+            const float* pe = reinterpret_cast<const float*>(se);
+            const float* pl = reinterpret_cast<const float*>(sl);
+            const float xe = pe[idx], ye = pe[yoff + idx];
+            const float xl = has_leave ? pl[idx] : 0.f, yl = has_leave ? pl[yoff + idx] : 0.f;
+            Xe = __float_as_int(fmaf(xe - qmx, row_ok ? fse_x : 0.f, 12582912.0f)) - 0x4B400000;
+            Ye = __float_as_int(fmaf(ye - qmy, row_ok ? fse_y : 0.f, 12582912.0f)) - 0x4B400000;
+            Xl = __float_as_int(fmaf(xl - qmx, row_ok ? fsl_x : 0.f, 12582912.0f)) - 0x4B400000;
+            Yl = __float_as_int(fmaf(yl - qmy, row_ok ? fsl_y : 0.f, 12582912.0f)) - 0x4B400000;
+          } else {
+            const uint16_t* pe = reinterpret_cast<const uint16_t*>(se);
+            const uint16_t* pl = reinterpret_cast<const uint16_t*>(sl);
+            Xe = (ue && row_ok) ? (int)pe[idx] : 0;
+            Ye = (ue && row_ok) ? (int)pe[yoff + idx] : 0;
+            Xl = (ul && row_ok) ? (int)pl[idx] : 0;
+            Yl = (ul && row_ok) ? (int)pl[yoff + idx] : 0;
+          }
+          const int D = (int)((uint32_t)Xe - (uint32_t)Xl), S = (int)((uint32_t)Xe + (uint32_t)Xl);
+          const int Dy = (int)((uint32_t)Ye - (uint32_t)Yl), Sy = (int)((uint32_t)Ye + (uint32_t)Yl);
+          P0 += (uint32_t)D;
+          P1 += (uint32_t)Dy;
+          P2 += (uint64_t)((long long)D * S);
+          P3 += (uint64_t)((long long)Dy * Sy);
+          P4 += (uint64_t)((long long)D * Ye) + (uint64_t)((long long)Xl * Dy);
+          if (r <= TY - 2) {
+            S0[r + 1] = P0; S1[r + 1] = P1; S2[r + 1] = P2; S3[r + 1] = P3; S4[r + 1] = P4;
+          }
+          if (r >= KY - 1) {
+            const int y = r - (KY - 1);
+            const uint32_t v0 = P0 - (y >= 1 ? S0[y] : 0u), v1 = P1 - (y >= 1 ? S1[y] : 0u);
+            const uint64_t v2 = P2 - (y >= 1 ? S2[y] : 0ull), v3 = P3 - (y >= 1 ? S3[y] : 0ull);
+            const uint64_t v4 = P4 - (y >= 1 ? S4[y] : 0ull);
+            const int base = y * G::VSP + c;
+            const int plane = TY * G::VSP;
+            VS[0 * plane + base] = v0;
+            VS[1 * plane + base] = v1;
+            VS[2 * plane + base] = (uint32_t)v2;
+            VS[3 * plane + base] = (uint32_t)(v2 >> 32);
+            VS[4 * plane + base] = (uint32_t)v3;
+            VS[5 * plane + base] = (uint32_t)(v3 >> 32);
+            VS[6 * plane + base] = (uint32_t)v4;
+            VS[7 * plane + base] = (uint32_t)(v4 >> 32);
+          }
+        }
+        (void)fsl_y;
+      }
+      __syncthreads();
+
+      // horizontal pass: warp -> 2 output rows, lane -> 4 output columns
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        const int y = warp * 2 + a;
+        uint32_t Q0 = 0u, Q1 = 0u;
+        uint64_t Q2 = 0ull, Q3 = 0ull, Q4 = 0ull;
+        uint32_t R0[4], R1[4];
+        uint64_t R2[4], R3[4], R4[4];
+        const int plane = TY * G::VSP;
+#pragma unroll
+        for (int e = 0; e < 4 + KX - 1; e++) {
+          const int cidx = y * G::VSP + 4 * lane + e;
+          Q0 += VS[0 * plane + cidx];
+          Q1 += VS[1 * plane + cidx];
+          Q2 += (uint64_t)VS[2 * plane + cidx] | ((uint64_t)VS[3 * plane + cidx] << 32);
+          Q3 += (uint64_t)VS[4 * plane + cidx] | ((uint64_t)VS[5 * plane + cidx] << 32);
+          Q4 += (uint64_t)VS[6 * plane + cidx] | ((uint64_t)VS[7 * plane + cidx] << 32);
+          if (e <= 2) {
+            R0[e + 1] = Q0; R1[e + 1] = Q1; R2[e + 1] = Q2; R3[e + 1] = Q3; R4[e + 1] = Q4;
+          }
+          if (e >= KX - 1) {
+            const int c = e - (KX - 1);
+            V0[a][c] += Q0 - (c >= 1 ? R0[c] : 0u);
+            V1[a][c] += Q1 - (c >= 1 ? R1[c] : 0u);
+            V2[a][c] += Q2 - (c >= 1 ? R2[c] : 0ull);
+            V3[a][c] += Q3 - (c >= 1 ? R3[c] : 0ull);
+            V4[a][c] += Q4 - (c >= 1 ? R4[c] : 0ull);
+          }
+        }
+      }
+
+      // step 4 for the output plane whose window is complete
+      if (s >= p.kz - 1) {
+        const int zc = zc0 + (s - (p.kz - 1));
+        if (zc % p.sz == 0) {
+          const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;
+#pragma unroll
+          for (int a = 0; a < 2; a++) {
+            const int yc = y0 + warp * 2 + a;
+            if (yc >= p.H || yc % p.sy != 0) continue;
+            const int cy = min(yc + G::H2, p.H - 1) - max(yc - G::H1, 0) + 1;
+            float* orow = p.out + (long long)(zc / p.sz) * p.opz + (long long)(yc / p.sy) * p.opy;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+              const int xc = x0 + 4 * lane + c;
+              if (xc >= p.W || xc % p.sx != 0) continue;
+              const int cx = min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1;
+              const uint64_t n = (uint64_t)cz * (uint64_t)cy * (uint64_t)cx;
+              const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
+              const long long vx = (long long)(n * V2[a][c] - s0 * s0);
+              const long long vy = (long long)(n * V3[a][c] - s1 * s1);
+              const long long num = (long long)(n * V4[a][c] - s0 * s1);
+              orow[xc / p.sx] =
+                  clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+            }
+          }
+        }
+      }
+      __syncthreads();  // VS and the ring slots are reused next step
+    }
+  }
+}
+
+}  // namespace swc

@@ -25,4 +25,12 @@ cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
 int k1d_outputs_per_lane();
 cudaError_t k1d_launch(const K1DParams& p, int grid, size_t smem, cudaStream_t st);
 
+// 3-D (uint16 or float32), square in-plane windows ky = kx = k.
+struct Geo3DInfo {
+  int TY, TX, TYI, BXW, XH, VSP;
+};
+struct K3DParams;
+bool k3d_geometry(int k, Geo3DInfo* g);
+cudaError_t k3d_launch(int k, const K3DParams& p, int grid, size_t smem, cudaStream_t st);
+
 }  // namespace swc

@@ -14,6 +14,7 @@
 
 #include "../../include/swcorr.h"
 #include "hostapi.h"
+#include "k3d.cuh"
 #include "launch.h"
 
 using namespace swc;
@@ -93,6 +94,21 @@ swcorr_status encode_1d(CUtensorMap* m, CUtensorMapDataType dt, const void* base
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled (1-D) failed (CUresult %d)", (int)r);
+  return SWCORR_OK;
+}
+
+swcorr_status encode_3d(CUtensorMap* m, CUtensorMapDataType dt, int eb, const void* base, int64_t W, int64_t H,
+                        int64_t Z, int64_t py, int64_t pz, int box_w, int box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Z};
+  cuuint64_t strides[2] = {(cuuint64_t)(py * eb), (cuuint64_t)(pz * eb)};
+  cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SWCORR_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (CUresult %d)", (int)r);
   return SWCORR_OK;
 }
 
@@ -197,7 +213,7 @@ swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, con
 
 }  // namespace swc
 
-enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_BATCHED = 10 };
+enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_3D = 4, KIND_BATCHED = 10 };
 
 struct swcorr_plan_s {
   int kind = 0;
@@ -216,6 +232,9 @@ struct swcorr_plan_s {
   size_t smem = 0;
   // 1-D launch
   K1DParams k1{};
+  // 3-D launch
+  K3DParams k3{};
+  Geo3DInfo g3{};
   // tensor-map cache
   const void* cached_x = nullptr;
   const void* cached_y = nullptr;
@@ -304,6 +323,98 @@ static swcorr_status run_1d(swcorr_plan_s* p, const void* x, const void* y, floa
   return SWCORR_OK;
 }
 
+static swcorr_status plan_3d(swcorr_plan_s* p) {
+  K3DParams& k3 = p->k3;
+  if (p->k[1] != p->k[2])
+    return fail(SWCORR_ERR_UNSUPPORTED, "3-D windows need equal row and column sizes (got %d x %d)", p->k[1],
+                p->k[2]);
+  if (!k3d_geometry(p->k[2], &p->g3))
+    return fail(SWCORR_ERR_UNSUPPORTED, "3-D in-plane window %d has no kernel instance (1..15 odd)", p->k[2]);
+  const Geo3DInfo& g = p->g3;
+  k3.Z = (int)p->shape[0];
+  k3.H = (int)p->shape[1];
+  k3.W = (int)p->shape[2];
+  k3.kz = p->k[0];
+  k3.hz1 = (k3.kz - 1) / 2;
+  k3.hz2 = k3.kz / 2;
+  k3.sz = p->stride[0];
+  k3.sy = p->stride[1];
+  k3.sx = p->stride[2];
+  k3.OZ = (int)p->oshape[0];
+  k3.OY = (int)p->oshape[1];
+  k3.OX = (int)p->oshape[2];
+  k3.nyb = (k3.H + g.TY - 1) / g.TY;
+  k3.nxb = (k3.W + g.TX - 1) / g.TX;
+  k3.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
+  const double n = (double)p->k[0] * p->k[1] * p->k[2];
+  int qb = 22;
+  while (qb > 8 && 2.0 * std::log2(n) + 2.0 * qb >= 62.0) qb--;
+  k3.qbits = qb;
+  const int eb = k3.is_f32 ? 4 : 2;
+  const size_t slot = 2 * (((size_t)g.TYI * g.BXW * eb + 127) / 128 * 128);
+  p->smem = 4 * slot + (size_t)8 * g.TY * g.VSP * 4 + 32;
+  if (p->smem > (size_t)p->dev.smem_optin)
+    return fail(SWCORR_ERR_UNSUPPORTED, "3-D plan needs %zu B of shared memory", p->smem);
+  const int per_sm = std::max(1, std::min(4, (int)((220 * 1024) / (p->smem + 2048))));
+  const int slots = p->dev.sms * per_sm;
+  const int64_t F = (int64_t)k3.nyb * k3.nxb;
+  int TZ = (int)std::min<int64_t>(k3.Z, std::max<int64_t>(16, (k3.Z * F + 4 * slots - 1) / (4 * slots)));
+  TZ = std::max(1, TZ);
+  k3.TZ = TZ;
+  k3.nzb = (k3.Z + TZ - 1) / TZ;
+  k3.n_items = (int)(k3.nzb * F);
+  k3.opy = k3.OX;
+  k3.opz = (long long)k3.OY * k3.OX;
+  p->grid = std::min(k3.n_items, slots);
+  return SWCORR_OK;
+}
+
+static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                            const int64_t* out_pitch, cudaStream_t st) {
+  K3DParams& k3 = p->k3;
+  const int eb = (int)elem_size(p->dtype);
+  const int64_t py = in_pitch ? in_pitch[1] : k3.W;
+  const int64_t pz = in_pitch ? in_pitch[0] : (int64_t)k3.H * py;
+  if (in_pitch && in_pitch[2] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[2] must be 1");
+  if (py < k3.W || pz < (int64_t)k3.H * py) return fail(SWCORR_ERR_INVALID_ARG, "input pitches too small");
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & (eb - 1))
+    return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
+  // TMA needs 16-byte aligned bases and pitches; otherwise plain loads
+  const bool tma =
+      !(((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) || (py * eb) % 16 || (pz * eb) % 16);
+  k3.use_tma = tma ? 1 : 0;
+  k3.gx = x;
+  k3.gy = y;
+  k3.ipy = py;
+  k3.ipz = pz;
+  if (out_pitch) {
+    if (out_pitch[2] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "out_pitch[2] must be 1");
+    k3.opz = out_pitch[0];
+    k3.opy = out_pitch[1];
+  } else {
+    k3.opy = k3.OX;
+    k3.opz = (long long)k3.OY * k3.OX;
+  }
+  if (tma && (x != p->cached_x || y != p->cached_y || py != p->cached_pitch)) {
+    const CUtensorMapDataType dt = p->dtype == SWCORR_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                          : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    swcorr_status s1 = encode_3d(&k3.tmx, dt, eb, x, k3.W, k3.H, k3.Z, py, pz, p->g3.BXW, p->g3.TYI);
+    if (s1 == SWCORR_OK) s1 = encode_3d(&k3.tmy, dt, eb, y, k3.W, k3.H, k3.Z, py, pz, p->g3.BXW, p->g3.TYI);
+    if (s1 != SWCORR_OK) {
+      p->cached_x = p->cached_y = nullptr;
+      return s1;
+    }
+    p->cached_x = x;
+    p->cached_y = y;
+    p->cached_pitch = py;
+  }
+  k3.out = c;
+  k3.status = p->d_status;
+  cudaError_t e = k3d_launch(p->k[2], k3, p->grid, p->smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "3-D kernel launch");
+  return SWCORR_OK;
+}
+
 static swcorr_status plan_2d(swcorr_plan_s* p) {
   return setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0],
                   p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid);
@@ -364,6 +475,9 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
   } else if (ndim == 1) {
     tmp.kind = KIND_1D;
     st = plan_1d(&tmp);
+  } else if (ndim == 3) {
+    tmp.kind = KIND_3D;
+    st = plan_3d(&tmp);
   } else {
     st = fail(SWCORR_ERR_UNSUPPORTED, "ndim %d with dtype %s is not provided yet", ndim,
               dtype == SWCORR_U16 ? "u16" : "f32");
@@ -432,6 +546,9 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   switch (p->kind) {
     case KIND_2D_U16:
     case KIND_2D_F32: return run_2d(p, x, y, in_pitch, c, out_pitch, sums, st);
+    case KIND_3D:
+      if (sums) return fail(SWCORR_ERR_UNSUPPORTED, "3-D plans do not emit sums");
+      return run_3d(p, x, y, in_pitch, c, out_pitch, st);
     case KIND_1D:
       if (sums) return fail(SWCORR_ERR_UNSUPPORTED, "1-D plans do not emit sums");
       if ((in_pitch && in_pitch[0] != 1) || (out_pitch && out_pitch[0] != 1))

@@ -1,0 +1,66 @@
+"""GPU parity of the fused 3-D kernel against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_06507_gb300 import workloads as W
+from tests.gpu_util import score, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_1807_06507_gb300 import swcorr
+    swcorr.load()
+    return swcorr
+
+
+def run3(sw, x, y, k, stride=None):
+    dtype = "u16" if x.dtype == np.uint16 else "f32"
+    p = sw.Plan(x.shape, k, stride, dtype=dtype)
+    c = p.run(to_dev(x, torch), to_dev(y, torch))
+    torch.cuda.synchronize()
+    p.check_status()
+    out = c.cpu().numpy()
+    p.close()
+    return out
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+def test_halfspace_volume_small(sw, stride):
+    x, y = W.halfspace_volume_pair((40, 70, 300), seed=11)
+    ref, rx, ry = oracle.corr(x, y, 9, stride, relvar=True)
+    score(run3(sw, x, y, 9, stride), ref, rx, ry, exact_nan=False)
+
+
+@pytest.mark.parametrize("shape,k", [((12, 33, 260), (3, 5, 5)), ((9, 20, 140), (5, 3, 3)), ((1, 1, 1), 3),
+                                     ((5, 3, 200), 7), ((17, 9, 129), (1, 1, 1)), ((6, 30, 64), (9, 15, 15))])
+def test_u16_volumes_exact(sw, shape, k):
+    rng = np.random.default_rng(sum(shape))
+    x = rng.integers(0, 65536, shape).astype(np.uint16)
+    y = rng.integers(0, 65536, shape).astype(np.uint16)
+    x[:, : shape[1] // 2, : shape[2] // 3] = 9
+    score(run3(sw, x, y, k), oracle.corr(x, y, k))
+
+
+@pytest.mark.parametrize("stride", [(2, 1, 3), (1, 2, 2)])
+def test_f32_strides_and_offsets(sw, stride):
+    rng = np.random.default_rng(3)
+    x = (1e4 + rng.standard_normal((20, 40, 150))).astype(np.float32)
+    y = (0.5 * x + rng.standard_normal((20, 40, 150))).astype(np.float32)
+    ref, rx, ry = oracle.corr(x, y, (5, 7, 7), stride, relvar=True)
+    score(run3(sw, x, y, (5, 7, 7), stride), ref, rx, ry, exact_nan=False)
+
+
+def test_full_volume_stride2_and_sampled_stride1(sw):
+    x, y = W.halfspace_volume_pair()
+    c2 = run3(sw, x, y, 9, 2)
+    ref, rx, ry = oracle.corr(x, y, 9, 2, relvar=True)
+    score(c2, ref, rx, ry, exact_nan=False)
+    c1 = run3(sw, x, y, 9, 1)
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, c1.size, 1 << 18)
+    ref, rx, ry = oracle.corr(x, y, 9, 1, idx=idx, relvar=True)
+    score(c1.ravel()[idx], ref, rx, ry, exact_nan=False)
