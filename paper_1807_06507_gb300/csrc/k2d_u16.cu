@@ -14,7 +14,9 @@ __global__ void __launch_bounds__(32) k2d_u16_kernel(const __grid_constant__ K2D
   rg.PF = p.PF;
   rg.rx = reinterpret_cast<uint16_t*>(smem_raw);
   rg.ry = rg.rx + (size_t)p.NR * G::RWS;
-  rg.bar = reinterpret_cast<uint64_t*>(rg.ry + (size_t)p.NR * G::RWS);
+  rg.lx = rg.ry + (size_t)p.NR * G::RWS;
+  rg.ly = rg.lx + (size_t)p.NR * G::RWS;
+  rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
     fence_mbar_init();

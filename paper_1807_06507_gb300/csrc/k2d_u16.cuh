@@ -4,8 +4,10 @@
 // pass over HBM, for one work item = (column strip of 32*M centre columns)
 // x (TJ output rows), processed by one warp:
 //
-//  * Rows stream into a shared-memory ring by TMA (one 2-D box row per
-//    input row, zero fill outside the grid = the clipped border).
+//  * Rows stream into shared-memory rings by TMA (one 2-D box row per
+//    input row, zero fill outside the grid = the clipped border): the row
+//    entering the column window and, separately, the row leaving it (read
+//    again from L2 kh rows later), so the ring depth does not grow with kh.
 //  * Step 1 (products) is formed on the fly from the entering row e and the
 //    leaving row l = e - kh of each column: d = x_e - x_l, s = x_e + x_l,
 //    x_e^2 - x_l^2 = d*s, x_e y_e - x_l y_l = d_x y_e + x_l d_y.
@@ -63,10 +65,12 @@ struct Geo2D {
 };
 
 struct Ring2D {
-  uint16_t* rx;  // [NR][RWS]
-  uint16_t* ry;  // [NR][RWS]
-  uint64_t* bar; // [NR]
-  int NR;
+  uint16_t* rx;  // entering rows, [NR][RWS]
+  uint16_t* ry;
+  uint16_t* lx;  // leaving rows, [NR][RWS]
+  uint16_t* ly;
+  uint64_t* bar; // [NR]: one phase per (entering, leaving) pair
+  int NR;        // = PF + 1
   int PF;
 };
 
@@ -76,25 +80,21 @@ __device__ __forceinline__ uint32_t get16(const uint32_t* w, int idx) {
 }
 
 // Exact per-window recomputation (rare path): int64 sums over the window's
-// cells in the ring (cells outside the grid are zero there), Pearson in fp64.
-template <int M, int KW>
-__device__ __noinline__ float exact_window_u16(const Ring2D& rg, uint32_t q, int kh, int lane, int c, int n,
-                                               long long* out5) {
-  using G = Geo2D<M, KW>;
+// in-grid cells read from global memory, Pearson in fp64.
+static __device__ __noinline__ float exact_window_u16(const Scene2D& sc, int rc, int cc, int kw, int n, long long* out5) {
+  const int w1 = (kw - 1) / 2, w2 = kw / 2;
+  const uint16_t* gx = (const uint16_t*)sc.gx;
+  const uint16_t* gy = (const uint16_t*)sc.gy;
   long long sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
-  for (int r = 0; r < kh; r++) {
-    const uint32_t slot = (q - (uint32_t)(kh - 1) + (uint32_t)r) % (uint32_t)rg.NR;
-    const uint16_t* px = rg.rx + (size_t)slot * G::RWS + M * lane + G::HALO + c - G::W1;
-    const uint16_t* py = rg.ry + (size_t)slot * G::RWS + M * lane + G::HALO + c - G::W1;
-    for (int u = 0; u < KW; u++) {
-      const long long a = px[u], b = py[u];
+  for (int r = max(rc - sc.h1, 0); r <= min(rc + sc.h2, sc.H - 1); r++)
+    for (int c = max(cc - w1, 0); c <= min(cc + w2, sc.W - 1); c++) {
+      const long long a = gx[(long long)r * sc.in_pitch + c], b = gy[(long long)r * sc.in_pitch + c];
       sx += a;
       sy += b;
       sxx += a * a;
       syy += b * b;
       sxy += a * b;
     }
-  }
   if (out5) {
     out5[0] = sx; out5[1] = sy; out5[2] = sxx; out5[3] = syy; out5[4] = sxy;
   }
@@ -102,9 +102,9 @@ __device__ __noinline__ float exact_window_u16(const Ring2D& rg, uint32_t q, int
   const long long vy = (long long)n * syy - sy * sy;
   const long long num = (long long)n * sxy - sx * sy;
   if (vx == 0 || vy == 0) return __int_as_float(0x7fc00000);
-  double cc = (double)num / sqrt((double)vx * (double)vy);
-  cc = fmin(fmax(cc, -1.0), 1.0);
-  return (float)cc;
+  double cv = (double)num / sqrt((double)vx * (double)vy);
+  cv = fmin(fmax(cv, -1.0), 1.0);
+  return (float)cv;
 }
 
 // Plain-load row loader (for row pitches that are not a multiple of 16 bytes,
@@ -172,32 +172,44 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   const uint32_t NR = (uint32_t)rg.NR;
   const int PF = rg.PF;
 
-  auto issue = [&](uint32_t s, int row) {
+  // entering row i (and, once i >= kh, leaving row i - kh) into slot s
+  auto issue = [&](uint32_t s, int i) {
+    const int row = t0 + i;
+    const bool lv = i >= sc.kh;
     if (!TMA) {
       ldg_row_u16<G::RW>(rg.rx + (size_t)s * G::RWS, (const uint16_t*)sc.gx, sc.in_pitch, row, xs, sc.H, sc.W,
                          lane);
       ldg_row_u16<G::RW>(rg.ry + (size_t)s * G::RWS, (const uint16_t*)sc.gy, sc.in_pitch, row, xs, sc.H, sc.W,
                          lane);
+      if (lv) {
+        ldg_row_u16<G::RW>(rg.lx + (size_t)s * G::RWS, (const uint16_t*)sc.gx, sc.in_pitch, row - sc.kh, xs, sc.H,
+                           sc.W, lane);
+        ldg_row_u16<G::RW>(rg.ly + (size_t)s * G::RWS, (const uint16_t*)sc.gy, sc.in_pitch, row - sc.kh, xs, sc.H,
+                           sc.W, lane);
+      }
       return;
     }
     uint64_t* b = rg.bar + s;
-    mbar_arrive_expect_tx(b, 2u * G::RW * 2u);
+    mbar_arrive_expect_tx(b, (lv ? 2u : 1u) * 2u * G::RW * 2u);
+    auto row_boxes = [&](uint16_t* dx, uint16_t* dy, int r) {
 #pragma unroll
-    for (int q = 0; q < G::NMAIN; q++) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, row, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, row, b);
-    }
-    if (G::TAIL > 0) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, row, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, row, b);
-    }
+      for (int q = 0; q < G::NMAIN; q++) {
+        tma_load_2d(dx + q * 256, sc.tmx, xs + q * 256, r, b);
+        tma_load_2d(dy + q * 256, sc.tmy, xs + q * 256, r, b);
+      }
+      if (G::TAIL > 0) {
+        tma_load_2d(dx + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, r, b);
+        tma_load_2d(dy + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, r, b);
+      }
+    };
+    row_boxes(rg.rx + (size_t)s * G::RWS, rg.ry + (size_t)s * G::RWS, row);
+    if (lv) row_boxes(rg.lx + (size_t)s * G::RWS, rg.ly + (size_t)s * G::RWS, row - sc.kh);
   };
 
-  // Ring bookkeeping without divisions in the row loop: slot of the entering
-  // row, its mbarrier phase, the leaving row's slot and the prefetch slot.
+  // Ring bookkeeping without divisions in the row loop: slot of row i, its
+  // mbarrier phase, and the prefetch slot.
   uint32_t s = seq % NR;
   uint32_t lap = (seq / NR) & 1u;
-  uint32_t sl = (s + NR - (uint32_t)sc.kh % NR) % NR;
   uint32_t sp = (s + (uint32_t)PF) % NR;
   {
     const int npre = min(PF, nrows);
@@ -205,7 +217,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       if (TMA) fence_proxy_async_smem();
       uint32_t si = s;
       for (int i = 0; i < npre; i++) {
-        issue(si, t0 + i);
+        issue(si, i);
         si = (si + 1 == NR) ? 0u : si + 1;
       }
     }
@@ -239,7 +251,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     __syncwarp();
     if (i + PF < nrows && (!TMA || lane == 0)) {
       if (TMA) fence_proxy_async_smem();
-      issue(sp, t0 + i + PF);
+      issue(sp, i + PF);
     }
     sp = (sp + 1 == NR) ? 0u : sp + 1;
     if (!TMA) {
@@ -268,8 +280,8 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
         ye[4 * h] = b.x; ye[4 * h + 1] = b.y; ye[4 * h + 2] = b.z; ye[4 * h + 3] = b.w;
       }
       if (has_leave) {
-        const uint16_t* pl = rg.rx + (size_t)sl * G::RWS + M * lane + G::CH0 * 8;
-        const uint16_t* ql = rg.ry + (size_t)sl * G::RWS + M * lane + G::CH0 * 8;
+        const uint16_t* pl = rg.lx + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
+        const uint16_t* ql = rg.ly + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
 #pragma unroll
         for (int h = 0; h < G::NCH; h++) {
           const uint4 a = *reinterpret_cast<const uint4*>(pl + 8 * h);
@@ -314,10 +326,8 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       }
     }
 
-    const uint32_t qrow = seq + (uint32_t)i;  // ring sequence number of this entering row
     s = (s + 1 == NR) ? 0u : s + 1;
     if (s == 0u) lap ^= 1u;
-    sl = (sl + 1 == NR) ? 0u : sl + 1;
 
     // Step 4 for the output row whose window is now complete.
     if (until_out == 0) {
@@ -388,7 +398,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
               }
             } else {
               // rare: sums that may not be exact in 32 bits, recomputed exactly
-              cv = exact_window_u16<M, KW>(rg, qrow, sc.kh, lane, c, (int)n, s5);
+              cv = exact_window_u16(sc, rc, cc, KW, (int)n, s5);
               atomicAdd(status + ST_FALLBACK, 1u);
             }
             orow[jc] = cv;

@@ -25,6 +25,12 @@ cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
 int k1d_outputs_per_lane();
 cudaError_t k1d_launch(const K1DParams& p, int grid, size_t smem, cudaStream_t st);
 
+// Batched 2-D uint16: ring row stride, one-time attribute set-up, launch.
+int kbatched_ring_row();
+const void* kbatched_kernel_ptr();
+cudaError_t kbatched_prepare();
+cudaError_t kbatched_launch(const KBatchParams& p, int grid, size_t smem, cudaStream_t st);
+
 // 3-D (uint16 or float32), square in-plane windows ky = kx = k.
 struct Geo3DInfo {
   int TY, TX, TYI, BXW, XH, VSP;

@@ -148,11 +148,13 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
   const uint64_t n = (uint64_t)kh * (uint64_t)kw;
   sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
   sc.qbits = n <= 512 ? 22 : 21;  // n^2 * (2^qbits)^2 < 2^63
+  // uint16: rings of entering and leaving rows, PF + 1 slots each; float32:
+  // one ring holding the column window plus the prefetch
   const int PF = f32 ? 3 : 4;
-  const int NR = kh + 1 + PF;
+  const int NR = f32 ? kh + 1 + PF : PF + 1;
   k2->NR = NR;
   k2->PF = PF;
-  const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 2 + (size_t)NR * 8;
+  const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 2 * (f32 ? 1 : 2) + (size_t)NR * 8;
   if (smem > (size_t)dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, smem);
   // one wave of work items over the resident warps
@@ -241,6 +243,13 @@ struct swcorr_plan_s {
   int64_t cached_pitch = -1;
   // device status block
   uint32_t* d_status = nullptr;
+  // batched plans: device block (scenes, tensor maps, items, counter), graph
+  void* d_batch = nullptr;
+  KBatchParams kb{};
+  int64_t batched_outputs = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
   // staging for host runs
   void* d_x = nullptr;
   void* d_y = nullptr;
@@ -248,6 +257,7 @@ struct swcorr_plan_s {
 };
 
 static int64_t n_outputs(const swcorr_plan_s* p) {
+  if (p->kind == KIND_BATCHED) return p->batched_outputs;
   int64_t n = 1;
   for (int d = 0; d < p->ndim; d++) n *= p->oshape[d];
   return n;
@@ -624,6 +634,10 @@ int64_t swcorr_plan_fallbacks(swcorr_plan p) {
 
 void swcorr_plan_destroy(swcorr_plan p) {
   if (!p) return;
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->d_batch);
   cudaFree(p->d_status);
   cudaFree(p->d_x);
   cudaFree(p->d_y);
@@ -634,18 +648,157 @@ void swcorr_plan_destroy(swcorr_plan p) {
 swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes, swcorr_dtype dtype,
                                   uint32_t flags) {
   g_last_error.clear();
-  if (out) *out = nullptr;
-  (void)scenes;
-  (void)n_scenes;
-  (void)dtype;
-  (void)flags;
-  return fail(SWCORR_ERR_UNSUPPORTED, "batched plans are not provided yet");
+  if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!scenes || n_scenes < 1) return fail(SWCORR_ERR_INVALID_ARG, "need at least one scene");
+  if (dtype != SWCORR_U16) return fail(SWCORR_ERR_UNSUPPORTED, "batched plans take uint16 scenes");
+  if (flags != 0) return fail(SWCORR_ERR_INVALID_ARG, "batched plans take no flags");
+  DeviceInfo dev;
+  swcorr_status st = device_info(&dev);
+  if (st != SWCORR_OK) return st;
+  cudaError_t e = kbatched_prepare();
+  if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
+
+  // per-scene set-up on the host
+  std::vector<Scene2D> sc(n_scenes);
+  std::vector<CUtensorMap> maps(4 * (size_t)n_scenes);
+  std::vector<double> cost(n_scenes);
+  int64_t outputs = 0;
+  for (int i = 0; i < n_scenes; i++) {
+    const swcorr_scene& s = scenes[i];
+    if (s.shape[0] < 1 || s.shape[1] < 1 || s.shape[0] > (1ll << 31) - 1024 || s.shape[1] > (1ll << 31) - 1024)
+      return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad shape", i);
+    if (s.k[0] < 1 || s.k[1] < 1) return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad window", i);
+    Geo2DInfo g;
+    if (!k2d_u16_geometry(s.k[1], &g) || g.M != 8)
+      return fail(SWCORR_ERR_UNSUPPORTED, "scene %d: window width %d has no kernel instance (1..31 odd)", i, s.k[1]);
+    if (!s.x || !s.y || !s.c) return fail(SWCORR_ERR_INVALID_ARG, "scene %d: NULL pointer", i);
+    if (s.in_pitch < s.shape[1] || s.out_pitch < s.shape[1])
+      return fail(SWCORR_ERR_INVALID_ARG, "scene %d: pitch smaller than the row", i);
+    if (((reinterpret_cast<uintptr_t>(s.x) | reinterpret_cast<uintptr_t>(s.y)) & 15) || (s.in_pitch * 2) % 16)
+      return fail(SWCORR_ERR_ALIGNMENT, "scene %d: batched inputs need 16-byte aligned bases and row pitches", i);
+    Scene2D& q = sc[i];
+    q.H = (int)s.shape[0];
+    q.W = (int)s.shape[1];
+    q.kh = s.k[0];
+    q.h1 = (q.kh - 1) / 2;
+    q.h2 = q.kh / 2;
+    q.kw = s.k[1];
+    q.sy = q.sx = 1;
+    q.OH = q.H;
+    q.OW = q.W;
+    q.n_strips = (q.W + 32 * g.M - 1) / (32 * g.M);
+    q.TJ = std::min(q.OH, std::max(64, 4 * q.kh));
+    q.n_rb = (q.OH + q.TJ - 1) / q.TJ;
+    const uint64_t n = (uint64_t)q.kh * (uint64_t)q.kw;
+    q.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
+    q.gx = s.x;
+    q.gy = s.y;
+    q.in_pitch = s.in_pitch;
+    q.out = s.c;
+    q.out_pitch = s.out_pitch;
+    q.sums = nullptr;
+    q.vec_store = ((reinterpret_cast<uintptr_t>(s.c) & 15) == 0 && (s.out_pitch % 4) == 0) ? 1 : 0;
+    st = encode_2d(&maps[4 * i + 0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.x, q.W, q.H, s.in_pitch, 256);
+    if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.y, q.W, q.H, s.in_pitch, 256);
+    if (st == SWCORR_OK && g.TAIL > 0) {
+      st = encode_2d(&maps[4 * i + 2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.x, q.W, q.H, s.in_pitch, g.TAIL);
+      if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 3], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.y, q.W, q.H, s.in_pitch, g.TAIL);
+    }
+    if (st != SWCORR_OK) return st;
+    cost[i] = (double)(q.TJ + q.kh - 1) * (8 + q.kw - 1 + 16);
+    outputs += (int64_t)q.H * q.W;
+  }
+  // work items, scenes with the costliest items first
+  std::vector<int> order(n_scenes);
+  for (int i = 0; i < n_scenes; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<BatchItem> items;
+  for (int i : order)
+    for (int rb = 0; rb < sc[i].n_rb; rb++)
+      for (int strip = 0; strip < sc[i].n_strips; strip++) items.push_back(BatchItem{i, strip, rb, 0});
+  if (items.size() > (size_t)0x7fffffff) return fail(SWCORR_ERR_UNSUPPORTED, "too many work items");
+
+  // one device block: maps (64-byte aligned), scenes, items, counter
+  const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
+  const size_t sc_off = (maps_bytes + 255) / 256 * 256;
+  const size_t it_off = sc_off + (n_scenes * sizeof(Scene2D) + 255) / 256 * 256;
+  const size_t ctr_off = it_off + (items.size() * sizeof(BatchItem) + 255) / 256 * 256;
+  const size_t total = ctr_off + 256;
+  swcorr_plan_s* p = new (std::nothrow) swcorr_plan_s();
+  if (!p) return fail(SWCORR_ERR_OOM, "host allocation of the plan failed");
+  p->kind = KIND_BATCHED;
+  p->ndim = 2;
+  p->dtype = dtype;
+  p->dev = dev;
+  p->batched_outputs = outputs;
+  auto cleanup = [&](swcorr_status s) {
+    swcorr_plan_destroy(p);
+    return s;
+  };
+  if ((e = cudaMalloc(&p->d_batch, total)) != cudaSuccess)
+    return cleanup(e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "batched plan: out of device memory")
+                                                  : cuda_fail(e, "cudaMalloc(batched plan)"));
+  if ((e = cudaMalloc(&p->d_status, ST_WORDS * sizeof(uint32_t))) != cudaSuccess)
+    return cleanup(cuda_fail(e, "cudaMalloc(status)"));
+  unsigned char* base = static_cast<unsigned char*>(p->d_batch);
+  for (int i = 0; i < n_scenes; i++) {
+    sc[i].tmx = reinterpret_cast<const CUtensorMap*>(base) + 4 * i + 0;
+    sc[i].tmy = reinterpret_cast<const CUtensorMap*>(base) + 4 * i + 1;
+    sc[i].tmx_t = reinterpret_cast<const CUtensorMap*>(base) + 4 * i + 2;
+    sc[i].tmy_t = reinterpret_cast<const CUtensorMap*>(base) + 4 * i + 3;
+  }
+  if ((e = cudaMemcpy(base, maps.data(), maps_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(base + sc_off, sc.data(), n_scenes * sizeof(Scene2D), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(base + it_off, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemset(base + ctr_off, 0, 256)) != cudaSuccess ||
+      (e = cudaMemset(p->d_status, 0, ST_WORDS * sizeof(uint32_t))) != cudaSuccess)
+    return cleanup(cuda_fail(e, "batched plan upload"));
+  KBatchParams& kb = p->kb;
+  kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
+  kb.items = reinterpret_cast<const BatchItem*>(base + it_off);
+  kb.n_items = (int)items.size();
+  kb.PF = 4;
+  kb.NR = kb.PF + 1;
+  kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off);
+  kb.status = p->d_status;
+  p->smem = (size_t)4 * kb.NR * kbatched_ring_row() * 2 + (size_t)kb.NR * 8;
+  int per_sm = 0;
+  p->grid = dev.sms * 8;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(), 32, p->smem) == cudaSuccess &&
+      per_sm > 0)
+    p->grid = dev.sms * per_sm;
+  p->grid = (int)std::min<int64_t>(p->grid, kb.n_items);
+  *out = p;
+  return SWCORR_OK;
 }
 
 swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
-  (void)stream;
+  g_last_error.clear();
   if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
-  return fail(SWCORR_ERR_UNSUPPORTED, "batched plans are not provided yet");
+  if (p->kind != KIND_BATCHED) return fail(SWCORR_ERR_INVALID_ARG, "not a batched plan");
+  cudaError_t e;
+  if (!p->graph_exec) {
+    // capture {reset the work-queue counter; persistent kernel} once
+    if ((e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "create capture stream");
+    if ((e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "begin capture");
+    cudaError_t e1 = cudaMemsetAsync(p->kb.counter, 0, sizeof(uint32_t), p->cap_stream);
+    cudaError_t e2 = kbatched_launch(p->kb, p->grid, p->smem, p->cap_stream);
+    e = cudaStreamEndCapture(p->cap_stream, &p->graph);
+    if (e1 != cudaSuccess) return cuda_fail(e1, "capture counter reset");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "capture batched kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    if ((e = cudaGraphInstantiate(&p->graph_exec, p->graph, 0)) != cudaSuccess) {
+      p->graph_exec = nullptr;
+      return cuda_fail(e, "instantiate graph");
+    }
+  }
+  if ((e = cudaGraphLaunch(p->graph_exec, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess)
+    return cuda_fail(e, "graph launch");
+  return SWCORR_OK;
 }
 
 }  // extern "C"

@@ -34,37 +34,53 @@ def uniform_pair(shape=(512, 512), seed=seed_for(1)):
 
 # ------------------------------------------------------ 2-D night scene (u16)
 def _value_noise(rng, shape, period):
-    """Bilinear upsampling of a random lattice with the given period (pixels)."""
+    """Bilinear upsampling of a random lattice with the given period (pixels),
+    interpolated along columns first, then along rows (float32)."""
     h, w = shape
     gh, gw = h // period + 2, w // period + 2
-    lat = rng.random((gh, gw))
-    ry = np.arange(h) / period
-    rx = np.arange(w) / period
+    lat = rng.random((gh, gw), dtype=np.float32)
+    ry = np.arange(h, dtype=np.float32) / np.float32(period)
+    rx = np.arange(w, dtype=np.float32) / np.float32(period)
     iy = ry.astype(np.int64)
     ix = rx.astype(np.int64)
     fy = (ry - iy)[:, None]
     fx = (rx - ix)[None, :]
-    a = lat[iy][:, ix]
-    b = lat[iy][:, ix + 1]
-    c = lat[iy + 1][:, ix]
-    d = lat[iy + 1][:, ix + 1]
-    return (a * (1 - fx) + b * fx) * (1 - fy) + (c * (1 - fx) + d * fx) * fy
+    lx = lat[:, ix] * (1 - fx) + lat[:, ix + 1] * fx
+    return lx[iy] * (1 - fy) + lx[iy + 1] * fy
 
 
-def cloud_field(rng, shape, coverage=0.30):
+def _upsample(a, factor, shape):
+    """Bilinear upsampling of a coarse grid by an integer factor, cropped to shape."""
+    h, w = shape
+    ry = np.arange(h, dtype=np.float32) / np.float32(factor)
+    rx = np.arange(w, dtype=np.float32) / np.float32(factor)
+    iy = np.minimum(ry.astype(np.int64), a.shape[0] - 2)
+    ix = np.minimum(rx.astype(np.int64), a.shape[1] - 2)
+    fy = (ry - iy)[:, None]
+    fx = (rx - ix)[None, :]
+    lx = a[:, ix] * (1 - fx) + a[:, ix + 1] * fx
+    return lx[iy] * (1 - fy) + lx[iy + 1] * fy
+
+
+def cloud_field(rng, shape, coverage=0.30, coarse=4):
     """Smooth multi-octave value noise mapped to a [0,1] cloud opacity.
 
-    Octaves at periods 512/256/128/64 px with halving amplitudes, normalised to
-    [0,1]; the top `coverage` fraction becomes cloud with a linear ramp.
+    Octaves at periods 512/256/128/64 px with halving amplitudes, evaluated on
+    a grid `coarse` times sparser (the field is smooth at that scale) and
+    normalised to [0,1]; the top `coverage` fraction becomes cloud with a
+    linear ramp; the result is upsampled bilinearly to full resolution.
     """
-    p = np.zeros(shape)
-    amp = 1.0
+    h, w = shape
+    cs = (h // coarse + 2, w // coarse + 2)
+    p = np.zeros(cs, dtype=np.float32)
+    amp = np.float32(1.0)
     for period in (512, 256, 128, 64):
-        p += amp * _value_noise(rng, shape, period)
-        amp *= 0.5
-    p = (p - p.min()) / max(p.max() - p.min(), 1e-12)
+        p += amp * _value_noise(rng, cs, period // coarse)
+        amp *= np.float32(0.5)
+    p = (p - p.min()) / max(float(p.max() - p.min()), 1e-12)
     q = np.quantile(p, 1.0 - coverage)
-    return np.clip((p - q) / max(1.0 - q, 1e-12), 0.0, 1.0)
+    f = np.clip((p - q) / max(1.0 - q, 1e-12), 0.0, 1.0).astype(np.float32)
+    return _upsample(f, coarse, shape)
 
 
 def night_scene(shape=(3000, 4000), seed=seed_for(2), n_sources=None,
@@ -81,8 +97,8 @@ def night_scene(shape=(3000, 4000), seed=seed_for(2), n_sources=None,
     h, w = shape
     if n_sources is None:
         n_sources = int(round(2000 * h * w / 12e6))
-    vis = vis_mean + sd * rng.standard_normal(shape)
-    ir = ir_mean + sd * rng.standard_normal(shape)
+    vis = np.float32(vis_mean) + np.float32(sd) * rng.standard_normal(shape, dtype=np.float32)
+    ir = np.float32(ir_mean) + np.float32(sd) * rng.standard_normal(shape, dtype=np.float32)
     if n_sources > 0:
         ys = rng.integers(0, h, n_sources)
         xs = rng.integers(0, w, n_sources)
@@ -91,10 +107,10 @@ def night_scene(shape=(3000, 4000), seed=seed_for(2), n_sources=None,
             for dx in range(-3, 4):
                 yy, xx = ys + dy, xs + dx
                 ok = (yy >= 0) & (yy < h) & (xx >= 0) & (xx < w)
-                np.add.at(vis, (yy[ok], xx[ok]), peak[ok] * np.exp(-0.5 * (dy * dy + dx * dx)))
+                np.add.at(vis, (yy[ok], xx[ok]), (peak[ok] * np.exp(-0.5 * (dy * dy + dx * dx))).astype(np.float32))
     f = cloud_field(rng, shape)
-    vis += 3000.0 * f
-    ir -= 2500.0 * f
+    vis += np.float32(3000.0) * f
+    ir -= np.float32(2500.0) * f
     vis = np.clip(np.rint(vis), 0, 16383).astype(np.uint16)
     ir = np.clip(np.rint(ir), 0, 16383).astype(np.uint16)
     return vis, ir
