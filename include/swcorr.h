@@ -95,7 +95,10 @@ typedef struct swcorr_plan_s* swcorr_plan;
  *   ndim   : 1, 2 or 3.
  *   shape  : ndim extents, each >= 1.
  *   k      : ndim window sizes, each >= 1 (the contiguous dimension's window
- *            k[ndim-1] must be <= 31 for 2-D/3-D).
+ *            k[ndim-1] must be <= 31 for 2-D/3-D).  uint16 windows hold at
+ *            most 32768 in-bounds cells (SWCORR_ERR_UNSUPPORTED beyond);
+ *            float32 windows of more than 511 cells keep fewer fixed-point
+ *            bits per cell (n * 2^bits < 2^31, at most 22 bits).
  *   stride : ndim steps >= 1, or NULL for all ones.
  *   dtype  : SWCORR_U16 or SWCORR_F32 (x and y share it).
  *   border : SWCORR_BORDER_CLIP.

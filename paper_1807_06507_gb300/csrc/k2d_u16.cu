@@ -5,54 +5,20 @@
 
 namespace swc {
 
-template <int M, int KW, bool TMA>
-__global__ void __launch_bounds__(32) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
-  using G = Geo2D<M, KW>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Ring2D rg;
-  rg.NR = p.NR;
-  rg.PF = p.PF;
-  rg.rx = reinterpret_cast<uint16_t*>(smem_raw);
-  rg.ry = rg.rx + (size_t)p.NR * G::RWS;
-  rg.lx = rg.ry + (size_t)p.NR * G::RWS;
-  rg.ly = rg.lx + (size_t)p.NR * G::RWS;
-  rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
-    fence_mbar_init();
-    if (TMA) {
-      prefetch_tmap(&p.tmx);
-      prefetch_tmap(&p.tmy);
-      if (G::TAIL > 0) {
-        prefetch_tmap(&p.tmx_t);
-        prefetch_tmap(&p.tmy_t);
-      }
-    }
-  }
-  __syncwarp();
-  Scene2D sc = p.sc;
-  sc.tmx = &p.tmx;
-  sc.tmy = &p.tmy;
-  sc.tmx_t = &p.tmx_t;
-  sc.tmy_t = &p.tmy_t;
-  uint32_t seq = 0;
-  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-    const int rb = item / sc.n_strips;
-    const int strip = item - rb * sc.n_strips;
-    if (!process_item_2d_u16<M, KW, TMA>(sc, strip, rb, rg, seq, p.status)) return;
-  }
-}
+#ifndef SWC_K2D_WIDE
+#define SWC_K2D_WIDE false
+#endif
 
 template <int M, int KW, bool TMA>
 static cudaError_t launch_tma(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
   static bool attr_done = false;  // per-process; harmless to repeat
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k2d_u16_kernel<M, KW, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  k2d_u16_kernel<M, KW, TMA><<<grid, 32, smem, st>>>(p);
+  k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE><<<grid, 32, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -88,7 +54,10 @@ bool k2d_u16_geometry(int kw, Geo2DInfo* g) {
   }
 }
 
-cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+cudaError_t k2d_u16_launch_wide(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+
+static cudaError_t k2d_u16_launch_narrow(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st,
+                                         bool tma) {
   switch (kw) {
 #define X(M, KW) \
   case KW:       \
@@ -98,6 +67,10 @@ cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+  return p.sc.wide ? k2d_u16_launch_wide(kw, p, grid, smem, st, tma) : k2d_u16_launch_narrow(kw, p, grid, smem, st, tma);
 }
 
 }  // namespace swc

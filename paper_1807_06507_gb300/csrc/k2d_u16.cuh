@@ -36,6 +36,8 @@
 // variance is detected exactly.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kparams.h"
 
@@ -158,7 +160,11 @@ constexpr float TT_LIMIT = 4.0e18f;
 
 // Process one work item.  Returns false if a bounded wait gave up (the
 // caller must then exit; in-flight copies have been drained).
-template <int M, int KW, bool TMA>
+// WIDE = false: the certified 32-bit engine described above.  WIDE = true
+// (large windows, n = kh*kw > 64, where second moments routinely exceed
+// 2^32): the second-moment sums are exact 64-bit integers and step 4 is
+// evaluated exactly in int64, with no certificate.
+template <int M, int KW, bool TMA, bool WIDE = false>
 __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip, int rb, const Ring2D& rg,
                                                     uint32_t& seq, uint32_t* status) {
   using G = Geo2D<M, KW>;
@@ -238,11 +244,14 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     inv_c[c] = n_c[c] == (uint32_t)(sc.kh * KW) ? sc.inv_n : __float2uint_rz(4294967296.0f * __frcp_rn(fn_c[c]));
   }
 
-  uint32_t V[M][5];
+  using Acc = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+  uint32_t V[M][2];  // sum x, sum y
+  Acc VQ[M][3];      // sum x^2, sum y^2, sum xy
 #pragma unroll
-  for (int c = 0; c < M; c++)
-#pragma unroll
-    for (int k = 0; k < 5; k++) V[c][k] = 0u;
+  for (int c = 0; c < M; c++) {
+    V[c][0] = V[c][1] = 0u;
+    VQ[c][0] = VQ[c][1] = VQ[c][2] = (Acc)0;
+  }
   uint32_t mx2 = 0u, my2 = 0u;
   int until_out = sc.kh - 1;  // rows until the next output row is complete
   int jr = j0;
@@ -302,8 +311,10 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
 
     // Row pass on the entering-minus-leaving differences, then the running
     // column sums.
-    uint32_t P[5] = {0u, 0u, 0u, 0u, 0u};
-    uint32_t Pst[M][5];  // prefix after column e, kept for output e + 1
+    uint32_t P[2] = {0u, 0u};
+    Acc PQ[3] = {(Acc)0, (Acc)0, (Acc)0};
+    uint32_t Pst[M][2];  // prefix after column e, kept for output e + 1
+    Acc PQst[M][3];
 #pragma unroll
     for (int e = 0; e < G::NCOL; e++) {
       const uint32_t xe = get16(we, G::E0 + e), xl = get16(wl, G::E0 + e);
@@ -312,17 +323,27 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       const uint32_t dy = yv - ylv, sys = yv + ylv;
       P[0] += dx;
       P[1] += dy;
-      P[2] += dx * sxs;
-      P[3] += dy * sys;
-      P[4] += dx * yv + xl * dy;
+      if (WIDE) {
+        PQ[0] += (Acc)((long long)(int)dx * (int)sxs);
+        PQ[1] += (Acc)((long long)(int)dy * (int)sys);
+        PQ[2] += (Acc)((long long)(int)dx * (int)yv + (long long)(int)xl * (int)dy);
+      } else {
+        PQ[0] += (Acc)(dx * sxs);
+        PQ[1] += (Acc)(dy * sys);
+        PQ[2] += (Acc)(dx * yv + xl * dy);
+      }
       if (e >= KW - 1) {
         const int c = e - (KW - 1);
 #pragma unroll
-        for (int k = 0; k < 5; k++) V[c][k] += P[k] - (c >= 1 ? Pst[c - 1][k] : 0u);
+        for (int k = 0; k < 2; k++) V[c][k] += P[k] - (c >= 1 ? Pst[c - 1][k] : 0u);
+#pragma unroll
+        for (int k = 0; k < 3; k++) VQ[c][k] += PQ[k] - (c >= 1 ? PQst[c - 1][k] : (Acc)0);
       }
       if (e <= M - 2) {
 #pragma unroll
-        for (int k = 0; k < 5; k++) Pst[e][k] = P[k];
+        for (int k = 0; k < 2; k++) Pst[e][k] = P[k];
+#pragma unroll
+        for (int k = 0; k < 3; k++) PQst[e][k] = PQ[k];
       }
     }
 
@@ -330,7 +351,40 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     if (s == 0u) lap ^= 1u;
 
     // Step 4 for the output row whose window is now complete.
-    if (until_out == 0) {
+    if (WIDE && until_out == 0) {
+      until_out = sc.sy;
+      const int rc = jr * sc.sy;
+      const int cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
+      float* orow = sc.out + (long long)jr * sc.out_pitch;
+      float res[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        const uint64_t n = cnt_r == sc.kh ? (uint64_t)n_c[c] : (uint64_t)(n_c[c] / (uint32_t)sc.kh * (uint32_t)cnt_r);
+        const uint64_t s0 = V[c][0], s1 = V[c][1];
+        // exact in 64-bit arithmetic; a zero variance makes num 0 and c NaN
+        const long long vx = (long long)(n * (uint64_t)VQ[c][0] - s0 * s0);
+        const long long vy = (long long)(n * (uint64_t)VQ[c][1] - s1 * s1);
+        const long long num = (long long)(n * (uint64_t)VQ[c][2] - s0 * s1);
+        res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+        const int cc = cl + c;
+        if (sc.sums && cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) {
+          long long* s5 = sc.sums + 5ll * ((long long)jr * sc.OW + (sc.sx == 1 ? cc : cc / sc.sx));
+          s5[0] = (long long)s0; s5[1] = (long long)s1;
+          s5[2] = (long long)VQ[c][0]; s5[3] = (long long)VQ[c][1]; s5[4] = (long long)VQ[c][2];
+        }
+      }
+      if (fast_cols && cl + M <= sc.W) {
+#pragma unroll
+        for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const int cc = cl + c;
+          if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) orow[sc.sx == 1 ? cc : cc / sc.sx] = res[c];
+        }
+      }
+      jr++;
+    } else if (until_out == 0) {
       until_out = sc.sy;
       const int rc = jr * sc.sy;
       const uint32_t Mx = max(mx2 & 0xFFFFu, mx2 >> 16), My = max(my2 & 0xFFFFu, my2 >> 16);
@@ -356,7 +410,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
 #pragma unroll
         for (int c = 0; c < M; c++) {
           float tt;
-          res[c] = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n_c[c], fn_c[c],
+          res[c] = pearson_u16(V[c][0], V[c][1], (uint32_t)VQ[c][0], (uint32_t)VQ[c][1], (uint32_t)VQ[c][2], n_c[c], fn_c[c],
                                __umulhi(V[c][0], inv_c[c]), __umulhi(V[c][1], inv_c[c]), tt);
           ttmax = fmaxf(ttmax, tt);
         }
@@ -391,10 +445,12 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
             long long* s5 = sc.sums ? sc.sums + 5ll * ((long long)jr * sc.OW + jc) : nullptr;
             float cv = 0.0f, tt = TT_LIMIT;
             if (certified(Mx, V[c][0], My, V[c][1]))
-              cv = pearson_u16(V[c][0], V[c][1], V[c][2], V[c][3], V[c][4], n, fn, a, b, tt);
+              cv = pearson_u16(V[c][0], V[c][1], (uint32_t)VQ[c][0], (uint32_t)VQ[c][1], (uint32_t)VQ[c][2], n, fn, a, b,
+                               tt);
             if (tt < TT_LIMIT) {
               if (s5) {
-                s5[0] = V[c][0]; s5[1] = V[c][1]; s5[2] = V[c][2]; s5[3] = V[c][3]; s5[4] = V[c][4];
+                s5[0] = V[c][0]; s5[1] = V[c][1];
+                s5[2] = (uint32_t)VQ[c][0]; s5[3] = (uint32_t)VQ[c][1]; s5[4] = (uint32_t)VQ[c][2];
               }
             } else {
               // rare: sums that may not be exact in 32 bits, recomputed exactly
@@ -411,6 +467,45 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   }
   seq += (uint32_t)nrows;
   return true;
+}
+
+// One warp per CTA, persistent over the plan's work items.
+template <int M, int KW, bool TMA, bool WIDE>
+__global__ void __launch_bounds__(32) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
+  using G = Geo2D<M, KW>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Ring2D rg;
+  rg.NR = p.NR;
+  rg.PF = p.PF;
+  rg.rx = reinterpret_cast<uint16_t*>(smem_raw);
+  rg.ry = rg.rx + (size_t)p.NR * G::RWS;
+  rg.lx = rg.ry + (size_t)p.NR * G::RWS;
+  rg.ly = rg.lx + (size_t)p.NR * G::RWS;
+  rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
+    fence_mbar_init();
+    if (TMA) {
+      prefetch_tmap(&p.tmx);
+      prefetch_tmap(&p.tmy);
+      if (G::TAIL > 0) {
+        prefetch_tmap(&p.tmx_t);
+        prefetch_tmap(&p.tmy_t);
+      }
+    }
+  }
+  __syncwarp();
+  Scene2D sc = p.sc;
+  sc.tmx = &p.tmx;
+  sc.tmy = &p.tmy;
+  sc.tmx_t = &p.tmx_t;
+  sc.tmy_t = &p.tmy_t;
+  uint32_t seq = 0;
+  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    const int rb = item / sc.n_strips;
+    const int strip = item - rb * sc.n_strips;
+    if (!process_item_2d_u16<M, KW, TMA, WIDE>(sc, strip, rb, rg, seq, p.status)) return;
+  }
 }
 
 }  // namespace swc

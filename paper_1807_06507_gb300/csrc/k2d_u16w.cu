@@ -1,0 +1,43 @@
+// k2d_u16w.cu -- instantiations of the fused 2-D uint16 kernel with 64-bit
+// second-moment sums (large windows).
+#include "k2d_u16.cuh"
+#include "launch.h"
+
+namespace swc {
+
+#define SWC_K2D_WIDE true
+
+template <int M, int KW, bool TMA>
+static cudaError_t launch_tma(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
+  static bool attr_done = false;  // per-process; harmless to repeat
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE><<<grid, 32, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int M, int KW>
+static cudaError_t launch_one(const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+  return tma ? launch_tma<M, KW, true>(p, grid, smem, st) : launch_tma<M, KW, false>(p, grid, smem, st);
+}
+
+#define SWC_K2D_CASES(X) X(8, 1) X(8, 3) X(8, 5) X(8, 7) X(8, 9) X(8, 11) X(8, 13) X(8, 15) X(8, 17) \
+  X(8, 19) X(8, 21) X(8, 23) X(8, 25) X(8, 27) X(8, 29) X(8, 31)
+
+cudaError_t k2d_u16_launch_wide(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+  switch (kw) {
+#define X(M, KW) \
+  case KW:       \
+    return launch_one<M, KW>(p, grid, smem, st, tma);
+    SWC_K2D_CASES(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swc

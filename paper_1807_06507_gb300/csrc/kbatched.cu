@@ -11,10 +11,10 @@
 
 namespace swc {
 
-template <int KW>
+template <int KW, bool WIDE>
 __device__ __forceinline__ bool run_item(const Scene2D& sc, int strip, int rb, const Ring2D& rg, uint32_t& seq,
                                          uint32_t* status) {
-  return process_item_2d_u16<8, KW, true>(sc, strip, rb, rg, seq, status);
+  return process_item_2d_u16<8, KW, true, WIDE>(sc, strip, rb, rg, seq, status);
 }
 
 __global__ void __launch_bounds__(32) kbatched_kernel(const __grid_constant__ KBatchParams p) {
@@ -44,13 +44,21 @@ __global__ void __launch_bounds__(32) kbatched_kernel(const __grid_constant__ KB
     const BatchItem it = p.items[item];
     const Scene2D sc = p.scenes[it.scene];
     bool ok = true;
-    switch (sc.kw) {
-#define X(KW)                                                     \
-  case KW:                                                        \
-    ok = run_item<KW>(sc, it.strip, it.rb, rg, seq, p.status);   \
+    // 32-bit engine for small windows (kw <= 9, kh*kw <= 64), 64-bit otherwise
+    const int key = sc.wide ? 100 + sc.kw : sc.kw;
+    switch (key) {
+#define X(KW)                                                           \
+  case KW:                                                              \
+    ok = run_item<KW, false>(sc, it.strip, it.rb, rg, seq, p.status);  \
     break;
-      X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31)
+#define XW(KW)                                                          \
+  case 100 + KW:                                                        \
+    ok = run_item<KW, true>(sc, it.strip, it.rb, rg, seq, p.status);   \
+    break;
+      X(1) X(3) X(5) X(7) X(9)
+      XW(1) XW(3) XW(5) XW(7) XW(9) XW(11) XW(13) XW(15) XW(17) XW(19) XW(21) XW(23) XW(25) XW(27) XW(29) XW(31)
 #undef X
+#undef XW
       default:
         if (lane == 0) atomicOr(p.status + ST_ERROR, ERRBIT_BAD_ARG);
         ok = false;

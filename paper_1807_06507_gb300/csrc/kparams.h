@@ -39,6 +39,7 @@ struct Scene2D {
   long long out_pitch;     // elements between output rows
   long long* sums;         // optional 5 int64 per output (debug / bit-exact tests)
   int qbits;               // float32 path: fixed-point magnitude bits (|X| < 2^qbits)
+  int wide;                // uint16 path: 64-bit second-moment sums (large windows)
 };
 
 struct K2DParams {

@@ -125,6 +125,20 @@ swcorr_status device_info(DeviceInfo* d) {
   return SWCORR_OK;
 }
 
+// Largest in-bounds window (cells) of the uint16 paths: the sum of a window's
+// values stays below 2^31 (n * 65535 < 2^31) and n^2 * var below 2^62.
+static constexpr uint64_t kMaxU16Cells = 32768;
+
+// Fixed-point magnitude bits of the float32 paths for windows of n cells:
+// |X| <= 2^qbits per cell, so n * 2^qbits < 2^31 keeps the window sums in
+// int32 and n^2 (2^qbits)^2 < 2^62 keeps the int64 finalize exact; at most
+// 22 bits (the rounding constant 1.5 * 2^23 of the conversion).
+static int f32_qbits(uint64_t n) {
+  int qb = 22;
+  while (qb > 1 && (double)n * std::ldexp(1.0, qb) >= 2147483648.0) qb--;
+  return qb;
+}
+
 // Geometry, launch shape and per-launch constants of the 2-D kernels.
 swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int kh, int kw, int sy, int sx,
                        Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out) {
@@ -133,6 +147,9 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
     return fail(SWCORR_ERR_UNSUPPORTED, "2-D %s: window width %d has no kernel instance (1..31 odd)",
                 f32 ? "float32" : "uint16", kw);
   const Geo2DInfo& g = *g2;
+  if (!f32 && (uint64_t)std::min(kh, H) * (uint64_t)std::min(kw, W) > kMaxU16Cells)
+    return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows are limited to %llu in-bounds cells (got %d x %d)",
+                (unsigned long long)kMaxU16Cells, kh, kw);
   Scene2D& sc = k2->sc;
   sc.H = H;
   sc.W = W;
@@ -147,7 +164,10 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
   sc.n_strips = (W + 32 * g.M - 1) / (32 * g.M);
   const uint64_t n = (uint64_t)kh * (uint64_t)kw;
   sc.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
-  sc.qbits = n <= 512 ? 22 : 21;  // n^2 * (2^qbits)^2 < 2^63
+  sc.qbits = f32_qbits(n);
+  // uint16 windows with more than 64 cells routinely have second moments
+  // beyond 2^32: use the 64-bit engine there
+  sc.wide = (!f32 && n > 64) ? 1 : 0;
   // uint16: rings of entering and leaving rows, PF + 1 slots each; float32:
   // one ring holding the column window plus the prefetch
   const int PF = f32 ? 3 : 4;
@@ -290,10 +310,10 @@ static swcorr_status plan_1d(swcorr_plan_s* p) {
   const int64_t need = align + (int64_t)(L - 1) * s + k + seg;  // span plus slack for the last segment
   k1.nbox = (int)((need + 255) / 256);
   k1.span = k1.nbox * 256;
-  // fixed point for float32: k^2 (2^qbits)^2 < 2^62
-  int qb = 22;
-  while (qb > 8 && 2.0 * std::log2((double)k) + 2.0 * qb >= 62.0) qb--;
-  k1.qbits = qb;
+  if (!k1.is_f32 && (uint64_t)std::min<int64_t>(k, N) > kMaxU16Cells)
+    return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows are limited to %llu in-bounds cells (got %d)",
+                (unsigned long long)kMaxU16Cells, k);
+  k1.qbits = f32_qbits((uint64_t)k);
   p->smem = (size_t)2 * k1.span * 4 + (size_t)L * 4 + 16;
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "1-D window %d with stride %d needs %zu B of shared memory", k, s, p->smem);
@@ -356,10 +376,11 @@ static swcorr_status plan_3d(swcorr_plan_s* p) {
   k3.nyb = (k3.H + g.TY - 1) / g.TY;
   k3.nxb = (k3.W + g.TX - 1) / g.TX;
   k3.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
-  const double n = (double)p->k[0] * p->k[1] * p->k[2];
-  int qb = 22;
-  while (qb > 8 && 2.0 * std::log2(n) + 2.0 * qb >= 62.0) qb--;
-  k3.qbits = qb;
+  const uint64_t n = (uint64_t)p->k[0] * p->k[1] * p->k[2];
+  k3.qbits = f32_qbits(n);
+  if (!k3.is_f32 && (uint64_t)std::min(k3.kz, k3.Z) * std::min(p->k[1], k3.H) * std::min(p->k[2], k3.W) > kMaxU16Cells)
+    return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows are limited to %llu in-bounds cells",
+                (unsigned long long)kMaxU16Cells);
   const int eb = k3.is_f32 ? 4 : 2;
   const size_t slot = 2 * (((size_t)g.TYI * g.BXW * eb + 127) / 128 * 128);
   p->smem = 4 * slot + (size_t)8 * g.TY * g.VSP * 4 + 32;
@@ -669,6 +690,9 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
     if (s.shape[0] < 1 || s.shape[1] < 1 || s.shape[0] > (1ll << 31) - 1024 || s.shape[1] > (1ll << 31) - 1024)
       return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad shape", i);
     if (s.k[0] < 1 || s.k[1] < 1) return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad window", i);
+    if ((uint64_t)std::min<int64_t>(s.k[0], s.shape[0]) * (uint64_t)std::min<int64_t>(s.k[1], s.shape[1]) > kMaxU16Cells)
+      return fail(SWCORR_ERR_UNSUPPORTED, "scene %d: uint16 windows are limited to %llu in-bounds cells", i,
+                  (unsigned long long)kMaxU16Cells);
     Geo2DInfo g;
     if (!k2d_u16_geometry(s.k[1], &g) || g.M != 8)
       return fail(SWCORR_ERR_UNSUPPORTED, "scene %d: window width %d has no kernel instance (1..31 odd)", i, s.k[1]);
@@ -699,6 +723,7 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
     q.out_pitch = s.out_pitch;
     q.sums = nullptr;
     q.vec_store = ((reinterpret_cast<uintptr_t>(s.c) & 15) == 0 && (s.out_pitch % 4) == 0) ? 1 : 0;
+    q.wide = (n > 64 || q.kw > 9) ? 1 : 0;  // the batched kernel has 32-bit bodies for kw <= 9 only
     st = encode_2d(&maps[4 * i + 0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.x, q.W, q.H, s.in_pitch, 256);
     if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.y, q.W, q.H, s.in_pitch, 256);
     if (st == SWCORR_OK && g.TAIL > 0) {

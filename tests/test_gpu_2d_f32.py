@@ -52,7 +52,8 @@ def test_night_scene_as_float32_full_size(sw):
 
 
 @pytest.mark.parametrize("shape,k", [((200, 300), 3), ((257, 530), 5), ((130, 600), 15), ((100, 300), 31),
-                                     ((41, 600), (7, 3)), ((90, 128), (3, 9)), ((20, 530), (9, 1))])
+                                     ((41, 600), (7, 3)), ((90, 128), (3, 9)), ((20, 530), (9, 1)),
+                                     ((130, 400), (21, 31)), ((150, 300), (60, 31))])
 def test_windows(sw, shape, k):
     rng = np.random.default_rng(shape[0] + shape[1])
     x = rng.standard_normal(shape).astype(np.float32)

@@ -68,6 +68,62 @@ def test_full_range_forces_exact_fallback(sw):
     score(c, oracle.corr(x, y, 7))
 
 
+@pytest.mark.parametrize("shape,k", [((140, 700), 15), ((120, 530), 31), ((90, 600), (3, 31)), ((150, 300), (31, 3)),
+                                     ((70, 515), (9, 9)), ((61, 333), (5, 13)), ((40, 260), (65, 1))])
+def test_wide_windows_full_range_exact(sw, shape, k):
+    # windows of more than 64 cells run the 64-bit engine: exact sums and c
+    # on full 16-bit data, with no per-window fallback
+    rng = np.random.default_rng(shape[0] * 7 + shape[1])
+    x = rng.integers(0, 65536, shape).astype(np.uint16)
+    y = (x // 2 + rng.integers(0, 32768, shape)).astype(np.uint16)
+    c, s, fb = run_u16(sw, x, y, k, sums=True)
+    assert fb == 0
+    assert np.array_equal(s, oracle.sums_u16(x, y, k))
+    score(c, oracle.corr(x, y, k))
+
+
+def test_wide_windows_strides_pitch_and_nan(sw):
+    x, y = W.night_scene((133, 611), seed=21)
+    x[10:70, 40:300] = 65535
+    y[80:130, 200:600] = 7
+    k = (11, 13)
+    c, s, fb = run_u16(sw, x, y, k, stride=(2, 3), sums=True)
+    assert fb == 0
+    assert np.array_equal(s, oracle.sums_u16(x, y, k, (2, 3)))
+    ref = oracle.corr(x, y, k, (2, 3))
+    assert np.isnan(ref).sum() > 1000
+    score(c, ref)
+    # a row pitch of 613 elements (not a multiple of 16 bytes): plain loads
+    xp = np.zeros((133, 613), np.uint16)
+    yp = np.zeros((133, 613), np.uint16)
+    xp[:, :611], yp[:, :611] = x, y
+    p = sw.Plan(x.shape, k, dtype="u16")
+    cp = p.run(to_dev(xp, torch), to_dev(yp, torch), in_pitch=(613, 1))
+    torch.cuda.synchronize()
+    p.check_status()
+    score(cp.cpu().numpy(), oracle.corr(x, y, k))
+
+
+def test_largest_uint16_window(sw):
+    # 1057 x 31 = 32767 cells of full-range data: the window sums reach
+    # 2^31 - 2^15 and the variances about 2^61, all still exact
+    rng = np.random.default_rng(1057)
+    shape = (1100, 40)
+    x = rng.integers(0, 65536, shape).astype(np.uint16)
+    x[:, :20] = 65535
+    y = rng.integers(0, 65536, shape).astype(np.uint16)
+    k = (1057, 31)
+    c, s, fb = run_u16(sw, x, y, k, sums=True)
+    assert fb == 0
+    assert np.array_equal(s, oracle.sums_u16(x, y, k))
+    score(c, oracle.corr(x, y, k))
+    with pytest.raises(sw.SwcorrError) as ei:
+        sw.Plan(shape, (1058, 31), dtype="u16")
+    assert ei.value.status == sw.ERR_UNSUPPORTED
+    # the limit counts in-bounds cells: a window taller than the grid is fine
+    sw.Plan((600, 40), (5001, 31), dtype="u16").close()
+
+
 @pytest.mark.parametrize("stride", [(2, 2), (3, 1), (1, 2), (2, 3)])
 def test_strides(sw, stride):
     x, y = W.night_scene((123, 700), seed=5)
