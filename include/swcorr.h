@@ -108,6 +108,59 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
                                  const int32_t* k, const int32_t* stride, swcorr_dtype dtype,
                                  swcorr_border border, uint32_t flags);
 
+/* Launch parameters of a plan, as chosen by the autotuner (support
+ * component; the paper has no counterpart).  0 in a field = the library's
+ * built-in default.
+ *   prefetch    : rows (2-D) in flight ahead of the row being summed: the
+ *                 depth of the shared-memory staging ring (1..8).
+ *   tile_rows   : least output rows (2-D) or planes (3-D) per work item, the
+ *                 height of a tile; the halo of kh - 1 rows is re-read per
+ *                 tile, so taller tiles read less but make fewer items.
+ *   ctas_per_sm : cap on resident one-warp CTAs per SM used to size the
+ *                 persistent grid (never above the kernel's occupancy).
+ * Results do not depend on these values (uint16 results are bit-identical;
+ * float32 results can differ in the last bits because the fixed-point
+ * reference of a lane follows its tile). */
+enum {
+  SWCORR_TUNE_MAX_PREFETCH = 8,
+  SWCORR_TUNE_MAX_TILE_ROWS = 4096,
+  SWCORR_TUNE_MAX_CTAS_PER_SM = 32
+};
+typedef struct {
+  int32_t prefetch;
+  int32_t tile_rows;
+  int32_t ctas_per_sm;
+  int32_t reserved[5]; /* must be 0 */
+} swcorr_tune;
+
+/* swcorr_plan_create with explicit launch parameters (tune != NULL) instead
+ * of the tune cache's entry for this device, ndim, dtype and k.  Values
+ * outside the ranges above give SWCORR_ERR_INVALID_ARG.  Used by the
+ * autotuner to time candidates. */
+swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t* shape,
+                                       const int32_t* k, const int32_t* stride, swcorr_dtype dtype,
+                                       swcorr_border border, uint32_t flags, const swcorr_tune* tune);
+
+/* The launch parameters a plan uses (after defaults and the cache). */
+swcorr_status swcorr_plan_tune(swcorr_plan p, swcorr_tune* out);
+
+/* Tune cache: a JSON file ({"format": "swcorr-tune-1", "entries": [...]},
+ * written by paper_1807_06507_gb300/autotune.py) that swcorr_plan_create and
+ * swcorr_plan_batched consult.  This call (re)reads `path` (NULL or "": no
+ * cache).  Without it, the first plan reads the file named by the
+ * SWCORR_TUNE_FILE environment variable, if set.  A file that cannot be read
+ * or does not parse is ignored as a whole (SWCORR_ERR_INVALID_ARG here, the
+ * built-in defaults apply).  Thread-safe; plans already created keep their
+ * parameters. */
+swcorr_status swcorr_set_tune_file(const char* path);
+
+/* Cache lookup without a device (tests, tools): 1 and *out filled if the
+ * loaded cache has an entry for (device, kind, ndim, k, dtype), else 0.
+ * device NULL matches any device; batched != 0 looks up the batched plan's
+ * entry (k ignored). */
+int swcorr_tune_lookup(const char* device, int batched, int ndim, const int32_t* k, swcorr_dtype dtype,
+                       swcorr_tune* out);
+
 /* Queue the correlation of device buffers x, y into device buffer c.
  *   x, y      : device pointers, 16-byte aligned, plan dtype.
  *   in_pitch  : ndim element pitches for x and y, or NULL (contiguous); the
@@ -146,6 +199,11 @@ typedef struct {
  * scene table; dtype must be SWCORR_U16. */
 swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
                                   swcorr_dtype dtype, uint32_t flags);
+
+/* swcorr_plan_batched with explicit launch parameters (see swcorr_tune;
+ * tile_rows is the least number of output rows per work item). */
+swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
+                                        swcorr_dtype dtype, uint32_t flags, const swcorr_tune* tune);
 
 /* Launch the batched plan on a stream (graph launch). */
 swcorr_status swcorr_run_batched(swcorr_plan p, void* stream);

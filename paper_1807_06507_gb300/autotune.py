@@ -1,0 +1,214 @@
+"""Autotuner: picks launch parameters per (device, plan kind, ndim, dtype, k)
+and writes them to the tune cache the library reads (swcorr_set_tune_file).
+
+For each configuration it times every candidate (prefetch depth x tile rows
+x CTAs per SM) with CUDA events on seeded synthetic inputs of that shape,
+checks that the candidate's output matches the default plan's output
+(bit-identical for uint16, within 1e-6 for float32), and keeps the fastest.
+
+    python -m paper_1807_06507_gb300.autotune [--out FILE] [--only NAME,...] [--reps N]
+
+The cache is JSON ({"format": "swcorr-tune-1", "entries": [...]}); entries
+for other devices or configurations already in FILE are kept.
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+from . import swcorr, workloads
+
+FORMAT = "swcorr-tune-1"
+
+
+def _dev(torch, a):
+    return torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda()
+
+
+def _time(torch, fn, reps, warm=3):
+    for i in range(warm):
+        fn(i)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn(i)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)
+    return statistics.median(ts)
+
+
+def _grid(**axes):
+    keys = list(axes)
+    for vals in itertools.product(*(axes[k] for k in keys)):
+        yield {k: v for k, v in zip(keys, vals) if v}
+
+
+# name -> (kind, dtype, shape, k, stride, candidate axes)
+CONFIGS = {
+    "2d_u16_k3": ("plain", "u16", (3000, 4000), (3, 3), None,
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[12, 16, 24, 32, 48], ctas_per_sm=[0, 12])),
+    "2d_u16_k5": ("plain", "u16", (3000, 4000), (5, 5), None,
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 20, 28, 40, 56], ctas_per_sm=[0, 12])),
+    "2d_u16_k7": ("plain", "u16", (3000, 4000), (7, 7), None,
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 21, 28, 40, 56], ctas_per_sm=[0, 12])),
+    "2d_u16_k9": ("plain", "u16", (3000, 4000), (9, 9), None,
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[24, 36, 48, 64], ctas_per_sm=[0])),
+    "2d_u16_k15": ("plain", "u16", (3000, 4000), (15, 15), None,
+                   dict(prefetch=[2, 3, 4, 6], tile_rows=[30, 45, 60, 90], ctas_per_sm=[0])),
+    "2d_u16_k31": ("plain", "u16", (3000, 4000), (31, 31), None,
+                   dict(prefetch=[2, 3, 4, 6], tile_rows=[62, 93, 124, 186], ctas_per_sm=[0])),
+    "2d_f32_k7": ("plain", "f32", (3000, 4000), (7, 7), None,
+                  dict(prefetch=[2, 3, 4], tile_rows=[16, 28, 40, 56], ctas_per_sm=[0])),
+    "1d_f32_k1001": ("plain", "f32", (1 << 26,), (1001,), None, dict(ctas_per_sm=[2, 3, 4, 5, 6, 8, 0])),
+    "3d_f32_k9": ("plain", "f32", (256, 512, 512), (9, 9, 9), None,
+                  dict(tile_rows=[8, 16, 32], ctas_per_sm=[1, 2, 3, 4])),
+    "batched_u16": ("batched", "u16", None, None, None,
+                    dict(prefetch=[3, 4, 6], tile_rows=[32, 64, 128])),
+}
+
+
+def _inputs(name, dtype, shape):
+    if len(shape) == 2:
+        x, y = workloads.night_scene(shape, seed=workloads.seed_for(2))
+        return (x, y) if dtype == "u16" else (x.astype(np.float32), y.astype(np.float32))
+    if len(shape) == 1:
+        return workloads.random_walk_pair(shape[0])
+    return workloads.halfspace_volume_pair(shape)
+
+
+def _same(a, b, dtype):
+    if dtype == "u16":
+        return np.array_equal(a, b, equal_nan=True)
+    fa, fb = np.isfinite(a), np.isfinite(b)
+    if not np.array_equal(fa, fb):
+        # a window whose spread is one fixed-point step can flip to NaN
+        # when the tile (and so the lane's fixed-point reference) changes
+        if np.mean(fa != fb) > 1e-6:
+            return False
+        fa = fa & fb
+    return bool(np.max(np.abs(a[fa] - b[fa]), initial=0.0) <= 1e-6)
+
+
+def tune_plain(torch, name, reps, log):
+    kind, dtype, shape, k, stride, axes = CONFIGS[name]
+    x, y = _inputs(name, dtype, shape)
+    nbytes = x.nbytes * 2 + x.size * 4
+    nsets = max(1, min(4, -(-(256 << 20) // nbytes)))  # rotate sets past the L2
+    sets = [(_dev(torch, x), _dev(torch, y)) for _ in range(nsets)]
+    base = swcorr.Plan(shape, k, stride, dtype=dtype, tune={})
+    c = torch.empty(base.oshape, dtype=torch.float32, device="cuda")
+    base.run(*sets[0], c=c)
+    torch.cuda.synchronize()
+    base.check_status()
+    ref = c.cpu().numpy()
+    t_def = _time(torch, lambda i: base.run(*sets[i % nsets], c=c), reps)
+    best = (t_def, base.tune())
+    log(f"{name}: default {base.tune()} {t_def:.1f} us")
+    base.close()
+    for cand in _grid(**axes):
+        try:
+            p = swcorr.Plan(shape, k, stride, dtype=dtype, tune=cand)
+        except swcorr.SwcorrError as e:
+            log(f"  {cand}: rejected ({e.detail})")
+            continue
+        p.run(*sets[0], c=c)
+        torch.cuda.synchronize()
+        p.check_status()
+        if not _same(c.cpu().numpy(), ref, dtype):
+            raise RuntimeError(f"{name}: candidate {cand} changed the results")
+        t = _time(torch, lambda i: p.run(*sets[i % nsets], c=c), reps)
+        log(f"  {cand}: {t:.1f} us")
+        if t < best[0]:
+            best = (t, p.tune())
+        p.close()
+    return {"kind": kind, "ndim": len(shape), "dtype": dtype, "k": list(k), **best[1],
+            "us": round(best[0], 2), "default_us": round(t_def, 2), "shape": list(shape)}
+
+
+def tune_batched(torch, name, reps, log):
+    kind, dtype, _, _, _, axes = CONFIGS[name]
+    scenes = workloads.batched_scenes(64)
+    dv = []
+    for s in scenes:
+        h, w = s.x.shape
+        wp = -(-w // 8) * 8
+        xp = np.zeros((h, wp), np.uint16)
+        yp = np.zeros((h, wp), np.uint16)
+        xp[:, :w], yp[:, :w] = s.x, s.y
+        dv.append((_dev(torch, xp)[:, :w], _dev(torch, yp)[:, :w],
+                   torch.empty((h, w), dtype=torch.float32, device="cuda"), s.k))
+    base = swcorr.BatchedPlan(dv, tune={})
+    base.run()
+    torch.cuda.synchronize()
+    base.check_status()
+    refs = [c.cpu().numpy() for _, _, c, _ in dv]
+    t_def = _time(torch, lambda i: base.run(), reps)
+    best = (t_def, base.tune())
+    log(f"{name}: default {base.tune()} {t_def:.1f} us")
+    base.close()
+    for cand in _grid(**axes):
+        p = swcorr.BatchedPlan(dv, tune=cand)
+        p.run()
+        torch.cuda.synchronize()
+        p.check_status()
+        if not all(_same(c.cpu().numpy(), r, dtype) for (_, _, c, _), r in zip(dv, refs)):
+            raise RuntimeError(f"{name}: candidate {cand} changed the results")
+        t = _time(torch, lambda i: p.run(), reps)
+        log(f"  {cand}: {t:.1f} us")
+        if t < best[0]:
+            best = (t, p.tune())
+        p.close()
+    return {"kind": kind, "ndim": 2, "dtype": dtype, "k": [0, 0], **best[1], "us": round(best[0], 2),
+            "default_us": round(t_def, 2), "scenes": len(scenes)}
+
+
+def merge(path, device, new_entries):
+    """Entries of `path` for other (device, kind, ndim, dtype, k) plus the new ones."""
+    old = []
+    if os.path.exists(path):
+        with open(path) as f:
+            old = json.load(f).get("entries", [])
+    key = lambda e: (e["device"], e.get("kind", "plain"), e["ndim"], e["dtype"], tuple(e["k"]))  # noqa: E731
+    new_keys = {key({**e, "device": device}) for e in new_entries}
+    kept = [e for e in old if key(e) not in new_keys]
+    return {"format": FORMAT, "entries": kept + [{"device": device, **e} for e in new_entries]}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--out", default=swcorr.DEFAULT_TUNE_FILE)
+    ap.add_argument("--only", default="", help="comma-separated configuration names")
+    ap.add_argument("--reps", type=int, default=15)
+    args = ap.parse_args(argv)
+    import torch
+    swcorr.load()
+    device = torch.cuda.get_device_name()
+    names = [n for n in CONFIGS if not args.only or n in args.only.split(",")]
+    entries = []
+    t0 = time.time()
+    for name in names:
+        fn = tune_batched if CONFIGS[name][0] == "batched" else tune_plain
+        e = fn(torch, name, args.reps, lambda s: print(s, flush=True))
+        print(f"{name}: best {e} ({time.time() - t0:.0f} s)", flush=True)
+        entries.append(e)
+        torch.cuda.empty_cache()
+    doc = merge(args.out, device, entries)
+    with open(args.out, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(f"wrote {len(doc['entries'])} entries to {args.out}")
+    swcorr.set_tune_file(args.out)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -55,6 +55,24 @@ bool k2d_u16_geometry(int kw, Geo2DInfo* g) {
 }
 
 cudaError_t k2d_u16_launch_wide(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+int k2d_u16_blocks_wide(int kw, size_t smem);
+
+int k2d_u16_blocks_per_sm(int kw, bool wide, size_t smem) {
+  if (wide) return k2d_u16_blocks_wide(kw, smem);
+  int b = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (kw) {
+#define X(M, KW)                                                                                      \
+  case KW:                                                                                            \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k2d_u16_kernel<M, KW, true, false>, 32, smem); \
+    break;
+    SWC_K2D_CASES(X)
+#undef X
+    default:
+      break;
+  }
+  return e == cudaSuccess ? b : 0;
+}
 
 static cudaError_t k2d_u16_launch_narrow(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st,
                                          bool tma) {

@@ -40,4 +40,20 @@ cudaError_t k2d_u16_launch_wide(int kw, const K2DParams& p, int grid, size_t sme
   }
 }
 
+int k2d_u16_blocks_wide(int kw, size_t smem) {
+  int b = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (kw) {
+#define X(M, KW)                                                                                     \
+  case KW:                                                                                           \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k2d_u16_kernel<M, KW, true, true>, 32, smem); \
+    break;
+    SWC_K2D_CASES(X)
+#undef X
+    default:
+      break;
+  }
+  return e == cudaSuccess ? b : 0;
+}
+
 }  // namespace swc

@@ -16,6 +16,9 @@ struct Geo2DInfo {
 // kw has no instance) and its launch.
 bool k2d_u16_geometry(int kw, Geo2DInfo* g);
 cudaError_t k2d_u16_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+// resident CTAs per SM of that instance (32-bit or 64-bit second moments)
+// with `smem` bytes of dynamic shared memory; 0 if the query fails
+int k2d_u16_blocks_per_sm(int kw, bool wide, size_t smem);
 
 // 2-D float32: same interface.
 bool k2d_f32_geometry(int kw, Geo2DInfo* g);

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -112,6 +113,20 @@ swcorr_status encode_3d(CUtensorMap* m, CUtensorMapDataType dt, int eb, const vo
   return SWCORR_OK;
 }
 
+// Device name (cached per device ordinal).
+static void device_name(int dev, char* out, size_t n) {
+  static std::mutex mu;
+  static std::map<int, std::string> names;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(dev);
+  if (it == names.end()) {
+    cudaDeviceProp prop;
+    std::string nm = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? std::string(prop.name) : std::string();
+    it = names.emplace(dev, nm).first;
+  }
+  std::snprintf(out, n, "%s", it->second.c_str());
+}
+
 swcorr_status device_info(DeviceInfo* d) {
   cudaError_t e = cudaGetDevice(&d->dev);
   if (e != cudaSuccess) return fail(SWCORR_ERR_NO_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
@@ -119,6 +134,7 @@ swcorr_status device_info(DeviceInfo* d) {
   cudaDeviceGetAttribute(&d->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->dev);
   cudaDeviceGetAttribute(&d->cc_major, cudaDevAttrComputeCapabilityMajor, d->dev);
   cudaDeviceGetAttribute(&d->cc_minor, cudaDevAttrComputeCapabilityMinor, d->dev);
+  device_name(d->dev, d->name, sizeof(d->name));
   if (d->cc_major != 10 || d->cc_minor != 3)
     return fail(SWCORR_ERR_NO_DEVICE, "libswcorr is built for sm_103a; device %d is sm_%d%d", d->dev, d->cc_major,
                 d->cc_minor);
@@ -141,7 +157,7 @@ static int f32_qbits(uint64_t n) {
 
 // Geometry, launch shape and per-launch constants of the 2-D kernels.
 swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int kh, int kw, int sy, int sx,
-                       Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out) {
+                       Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out, swcorr_tune* tune) {
   const bool f32 = dt == SWCORR_F32;
   if (!(f32 ? k2d_f32_geometry(kw, g2) : k2d_u16_geometry(kw, g2)))
     return fail(SWCORR_ERR_UNSUPPORTED, "2-D %s: window width %d has no kernel instance (1..31 odd)",
@@ -170,20 +186,30 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
   sc.wide = (!f32 && n > 64) ? 1 : 0;
   // uint16: rings of entering and leaving rows, PF + 1 slots each; float32:
   // one ring holding the column window plus the prefetch
-  const int PF = f32 ? 3 : 4;
+  const int PF = tune->prefetch > 0 ? tune->prefetch : (f32 ? 3 : 4);
   const int NR = f32 ? kh + 1 + PF : PF + 1;
   k2->NR = NR;
   k2->PF = PF;
   const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 2 * (f32 ? 1 : 2) + (size_t)NR * 8;
   if (smem > (size_t)dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, smem);
-  // one wave of work items over the resident warps
-  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (smem + 1024))));
+  int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (smem + 1024))));
+  if (!f32) {
+    const int b = k2d_u16_blocks_per_sm(kw, sc.wide != 0, smem);
+    if (b > 0) per_sm = std::min(per_sm, b);
+  }
+  if (tune->ctas_per_sm > 0) per_sm = std::min(per_sm, tune->ctas_per_sm);
   const int total = dev.sms * per_sm;
+  // one wave of work items over the resident warps, but tiles at least
+  // tile_rows tall (default 4 kh rows: the halo re-read stays below 25 %)
+  const int rows_min = tune->tile_rows > 0 ? tune->tile_rows : std::max(16, 4 * kh / std::max(1, sc.sy));
   int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
-  TJ = std::max(TJ, std::max(16, 4 * kh / std::max(1, sc.sy)));
+  TJ = std::max(TJ, rows_min);
   TJ = std::min(TJ, sc.OH);
   sc.TJ = TJ;
+  tune->prefetch = PF;
+  tune->tile_rows = rows_min;
+  tune->ctas_per_sm = per_sm;
   sc.n_rb = (sc.OH + TJ - 1) / TJ;
   k2->n_items = sc.n_rb * sc.n_strips;
   *grid_out = std::min(k2->n_items, total);
@@ -193,7 +219,8 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
 
 swcorr_status setup_2d_u16(const DeviceInfo& dev, int H, int W, int kh, int kw, int sy, int sx, Geo2DInfo* g2,
                            K2DParams* k2, size_t* smem_out, int* grid_out) {
-  return setup_2d(dev, SWCORR_U16, H, W, kh, kw, sy, sx, g2, k2, smem_out, grid_out);
+  swcorr_tune defaults{};
+  return setup_2d(dev, SWCORR_U16, H, W, kh, kw, sy, sx, g2, k2, smem_out, grid_out, &defaults);
 }
 
 // Pointers, pitches and (when the layout allows TMA) tensor maps of one 2-D
@@ -247,6 +274,7 @@ struct swcorr_plan_s {
   swcorr_dtype dtype = SWCORR_U16;
   uint32_t flags = 0;
   DeviceInfo dev;
+  swcorr_tune tune{};  // launch parameters in use (after defaults and the tune cache)
   // 2-D geometry and launch shape
   Geo2DInfo g2{};
   K2DParams k2{};
@@ -317,8 +345,12 @@ static swcorr_status plan_1d(swcorr_plan_s* p) {
   p->smem = (size_t)2 * k1.span * 4 + (size_t)L * 4 + 16;
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "1-D window %d with stride %d needs %zu B of shared memory", k, s, p->smem);
-  const int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
+  int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
+  if (p->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, p->tune.ctas_per_sm);
   p->grid = (int)std::min<int64_t>(k1.n_items, (int64_t)p->dev.sms * per_sm);
+  p->tune.prefetch = 1;
+  p->tune.tile_rows = 0;
+  p->tune.ctas_per_sm = per_sm;
   return SWCORR_OK;
 }
 
@@ -386,10 +418,12 @@ static swcorr_status plan_3d(swcorr_plan_s* p) {
   p->smem = 4 * slot + (size_t)8 * g.TY * g.VSP * 4 + 32;
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "3-D plan needs %zu B of shared memory", p->smem);
-  const int per_sm = std::max(1, std::min(4, (int)((220 * 1024) / (p->smem + 2048))));
+  int per_sm = std::max(1, std::min(4, (int)((220 * 1024) / (p->smem + 2048))));
+  if (p->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, p->tune.ctas_per_sm);
   const int slots = p->dev.sms * per_sm;
+  const int planes_min = p->tune.tile_rows > 0 ? p->tune.tile_rows : 16;
   const int64_t F = (int64_t)k3.nyb * k3.nxb;
-  int TZ = (int)std::min<int64_t>(k3.Z, std::max<int64_t>(16, (k3.Z * F + 4 * slots - 1) / (4 * slots)));
+  int TZ = (int)std::min<int64_t>(k3.Z, std::max<int64_t>(planes_min, (k3.Z * F + 4 * slots - 1) / (4 * slots)));
   TZ = std::max(1, TZ);
   k3.TZ = TZ;
   k3.nzb = (k3.Z + TZ - 1) / TZ;
@@ -397,6 +431,9 @@ static swcorr_status plan_3d(swcorr_plan_s* p) {
   k3.opy = k3.OX;
   k3.opz = (long long)k3.OY * k3.OX;
   p->grid = std::min(k3.n_items, slots);
+  p->tune.prefetch = 2;
+  p->tune.tile_rows = planes_min;
+  p->tune.ctas_per_sm = per_sm;
   return SWCORR_OK;
 }
 
@@ -448,7 +485,7 @@ static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, cons
 
 static swcorr_status plan_2d(swcorr_plan_s* p) {
   return setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0],
-                  p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid);
+                  p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid, &p->tune);
 }
 
 extern "C" {
@@ -473,6 +510,18 @@ const char* swcorr_version(void) { return "swcorr 0.1.0 sm_103a"; }
 
 swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shape, const int32_t* k,
                                  const int32_t* stride, swcorr_dtype dtype, swcorr_border border, uint32_t flags) {
+  return swcorr_plan_create_tuned(out, ndim, shape, k, stride, dtype, border, flags, nullptr);
+}
+
+swcorr_status swcorr_plan_tune(swcorr_plan p, swcorr_tune* out) {
+  if (!p || !out) return fail(SWCORR_ERR_INVALID_ARG, "plan and out must not be NULL");
+  *out = p->tune;
+  return SWCORR_OK;
+}
+
+swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t* shape, const int32_t* k,
+                                       const int32_t* stride, swcorr_dtype dtype, swcorr_border border,
+                                       uint32_t flags, const swcorr_tune* tune) {
   g_last_error.clear();
   if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -498,8 +547,15 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
     tmp.stride[d] = s;
     tmp.oshape[d] = (shape[d] + s - 1) / s;
   }
-  swcorr_status st = device_info(&tmp.dev);
+  swcorr_status st = tune_check(tune);
   if (st != SWCORR_OK) return st;
+  st = device_info(&tmp.dev);
+  if (st != SWCORR_OK) return st;
+  if (tune) {
+    tmp.tune = *tune;
+  } else if (!tune_lookup(tmp.dev.name, "plain", ndim, tmp.k, dtype, &tmp.tune)) {
+    tmp.tune = swcorr_tune{};
+  }
   if (ndim == 2) {
     tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
     st = plan_2d(&tmp);
@@ -668,15 +724,29 @@ void swcorr_plan_destroy(swcorr_plan p) {
 
 swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes, swcorr_dtype dtype,
                                   uint32_t flags) {
+  return swcorr_plan_batched_tuned(out, scenes, n_scenes, dtype, flags, nullptr);
+}
+
+swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
+                                        swcorr_dtype dtype, uint32_t flags, const swcorr_tune* tune) {
   g_last_error.clear();
   if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!scenes || n_scenes < 1) return fail(SWCORR_ERR_INVALID_ARG, "need at least one scene");
   if (dtype != SWCORR_U16) return fail(SWCORR_ERR_UNSUPPORTED, "batched plans take uint16 scenes");
   if (flags != 0) return fail(SWCORR_ERR_INVALID_ARG, "batched plans take no flags");
-  DeviceInfo dev;
-  swcorr_status st = device_info(&dev);
+  swcorr_status st = tune_check(tune);
   if (st != SWCORR_OK) return st;
+  DeviceInfo dev;
+  st = device_info(&dev);
+  if (st != SWCORR_OK) return st;
+  swcorr_tune tn{};
+  if (tune) {
+    tn = *tune;
+  } else if (!tune_lookup(dev.name, "batched", 2, nullptr, dtype, &tn)) {
+    tn = swcorr_tune{};
+  }
+  const int rows_min = tn.tile_rows > 0 ? tn.tile_rows : 64;
   cudaError_t e = kbatched_prepare();
   if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
 
@@ -712,7 +782,7 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
     q.OH = q.H;
     q.OW = q.W;
     q.n_strips = (q.W + 32 * g.M - 1) / (32 * g.M);
-    q.TJ = std::min(q.OH, std::max(64, 4 * q.kh));
+    q.TJ = std::min(q.OH, std::max(rows_min, 4 * q.kh));
     q.n_rb = (q.OH + q.TJ - 1) / q.TJ;
     const uint64_t n = (uint64_t)q.kh * (uint64_t)q.kw;
     q.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
@@ -784,7 +854,7 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
   kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
   kb.items = reinterpret_cast<const BatchItem*>(base + it_off);
   kb.n_items = (int)items.size();
-  kb.PF = 4;
+  kb.PF = tn.prefetch > 0 ? tn.prefetch : 4;
   kb.NR = kb.PF + 1;
   kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off);
   kb.status = p->d_status;
@@ -794,7 +864,16 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(), 32, p->smem) == cudaSuccess &&
       per_sm > 0)
     p->grid = dev.sms * per_sm;
+  else
+    per_sm = 8;
+  if (tn.ctas_per_sm > 0 && tn.ctas_per_sm < per_sm) {
+    per_sm = tn.ctas_per_sm;
+    p->grid = dev.sms * per_sm;
+  }
   p->grid = (int)std::min<int64_t>(p->grid, kb.n_items);
+  p->tune.prefetch = kb.PF;
+  p->tune.tile_rows = rows_min;
+  p->tune.ctas_per_sm = per_sm;
   *out = p;
   return SWCORR_OK;
 }

@@ -20,9 +20,16 @@ U16, F32 = 1, 2
 BORDER_CLIP = 0
 FLAG_EMIT_SUMS = 1
 
-EXPORTS = ("swcorr_plan_create", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_run_batched",
-           "swcorr_plan_status", "swcorr_plan_fallbacks", "swcorr_plan_outputs", "swcorr_plan_destroy",
-           "swcorr_status_string", "swcorr_last_error", "swcorr_version", "swcorr_run2d_u16_noalloc")
+EXPORTS = ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune", "swcorr_set_tune_file",
+           "swcorr_tune_lookup", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",
+           "swcorr_run_batched", "swcorr_plan_status", "swcorr_plan_fallbacks", "swcorr_plan_outputs",
+           "swcorr_plan_destroy", "swcorr_status_string", "swcorr_last_error", "swcorr_version",
+           "swcorr_run2d_u16_noalloc")
+
+# Tune cache shipped with the package (written by autotune.py); used unless
+# SWCORR_TUNE_FILE names another file.
+DEFAULT_TUNE_FILE = os.path.join(_HERE, "tune_cache.json")
+TUNE_FIELDS = ("prefetch", "tile_rows", "ctas_per_sm")
 
 
 class SwcorrError(RuntimeError):
@@ -36,6 +43,26 @@ class SceneStruct(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int64 * 2), ("k", ctypes.c_int32 * 2), ("x", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("in_pitch", ctypes.c_int64), ("c", ctypes.c_void_p),
                 ("out_pitch", ctypes.c_int64)]
+
+
+class TuneStruct(ctypes.Structure):
+    _fields_ = [("prefetch", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+def _tune_struct(tune):
+    if tune is None:
+        return None
+    t = TuneStruct()
+    for k, v in dict(tune).items():
+        if k not in TUNE_FIELDS:
+            raise KeyError(f"unknown tune field {k!r}")
+        setattr(t, k, int(v))
+    return t
+
+
+def _tune_dict(t):
+    return {k: int(getattr(t, k)) for k in TUNE_FIELDS}
 
 
 _lock = threading.Lock()
@@ -57,6 +84,15 @@ def load(path: str | None = None):
         vp = ctypes.c_void_p
         lib.swcorr_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64p, i32p, i32p, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_uint32]
+        tp = ctypes.POINTER(TuneStruct)
+        lib.swcorr_plan_create_tuned.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64p, i32p, i32p, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_uint32, tp]
+        lib.swcorr_plan_tune.argtypes = [vp, tp]
+        lib.swcorr_set_tune_file.argtypes = [ctypes.c_char_p]
+        lib.swcorr_tune_lookup.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, tp]
+        lib.swcorr_tune_lookup.restype = ctypes.c_int
+        lib.swcorr_plan_batched_tuned.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SceneStruct), ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_uint32, tp]
         lib.swcorr_run.argtypes = [vp, vp, vp, i64p, vp, i64p, vp, vp]
         lib.swcorr_run_host.argtypes = [vp, vp, vp, vp, vp]
         lib.swcorr_plan_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SceneStruct), ctypes.c_int,
@@ -76,9 +112,12 @@ def load(path: str | None = None):
         lib.swcorr_status_string.restype = ctypes.c_char_p
         lib.swcorr_last_error.restype = ctypes.c_char_p
         lib.swcorr_version.restype = ctypes.c_char_p
-        for name in ("swcorr_plan_create", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched",
+        for name in ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune", "swcorr_set_tune_file",
+                     "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",
                      "swcorr_run_batched", "swcorr_plan_status"):
             getattr(lib, name).restype = ctypes.c_int
+        if not os.environ.get("SWCORR_TUNE_FILE") and os.path.exists(DEFAULT_TUNE_FILE):
+            lib.swcorr_set_tune_file(DEFAULT_TUNE_FILE.encode())
         _lib = lib
         return lib
 
@@ -112,10 +151,27 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-class Plan:
-    """A plan for one grid shape (swcorr_plan_create / swcorr_run)."""
+def set_tune_file(path):
+    """(Re)load the tune cache from `path` (None: no cache)."""
+    _check(load().swcorr_set_tune_file(path.encode() if path else None))
 
-    def __init__(self, shape, k, stride=None, dtype="u16", flags=0):
+
+def tune_lookup(ndim, k, dtype, device=None, batched=False):
+    """The cached launch parameters for (device, ndim, k, dtype), or None."""
+    t = TuneStruct()
+    kk, _a = _arr([int(v) for v in np.broadcast_to(np.asarray(k), (ndim,))], ctypes.c_int32)
+    found = load().swcorr_tune_lookup(device.encode() if device else None, 1 if batched else 0, ndim, kk,
+                                      _dtype_code(dtype), ctypes.byref(t))
+    return _tune_dict(t) if found else None
+
+
+class Plan:
+    """A plan for one grid shape (swcorr_plan_create / swcorr_run).
+
+    tune: None (the tune cache or built-in defaults) or a dict with any of
+    prefetch, tile_rows, ctas_per_sm (swcorr_plan_create_tuned)."""
+
+    def __init__(self, shape, k, stride=None, dtype="u16", flags=0, tune=None):
         lib = load()
         self.shape = tuple(int(v) for v in shape)
         nd = len(self.shape)
@@ -128,7 +184,9 @@ class Plan:
         shp, _a = _arr(self.shape, ctypes.c_int64)
         kk, _b = _arr(self.k, ctypes.c_int32)
         ss, _c = _arr(self.stride, ctypes.c_int32)
-        _check(lib.swcorr_plan_create(ctypes.byref(h), nd, shp, kk, ss, self.dtype, BORDER_CLIP, self.flags))
+        t = _tune_struct(tune)
+        _check(lib.swcorr_plan_create_tuned(ctypes.byref(h), nd, shp, kk, ss, self.dtype, BORDER_CLIP, self.flags,
+                                            ctypes.byref(t) if t is not None else None))
         self._h = h
 
     @property
@@ -170,6 +228,12 @@ class Plan:
                                       ctypes.c_void_p(c.ctypes.data), _stream_ptr(stream)))
         return c
 
+    def tune(self) -> dict:
+        """Launch parameters the plan uses."""
+        t = TuneStruct()
+        _check(load().swcorr_plan_tune(self._h, ctypes.byref(t)))
+        return _tune_dict(t)
+
     def status(self) -> int:
         return load().swcorr_plan_status(self._h)
 
@@ -197,9 +261,9 @@ class Plan:
 class BatchedPlan:
     """One persistent launch over many 2-D uint16 scenes (swcorr_plan_batched)."""
 
-    def __init__(self, scenes, flags=0):
+    def __init__(self, scenes, flags=0, tune=None):
         """scenes: list of (x, y, c, (kh, kw)) with CUDA tensors; x/y rows may be
-        padded (strided views with unit last stride)."""
+        padded (strided views with unit last stride).  tune: as for Plan."""
         lib = load()
         arr = (SceneStruct * len(scenes))()
         self._keep = []
@@ -213,11 +277,18 @@ class BatchedPlan:
             s.out_pitch = int(c.stride(0))
             self._keep.append((x, y, c))
         h = ctypes.c_void_p()
-        _check(lib.swcorr_plan_batched(ctypes.byref(h), arr, len(scenes), U16, int(flags)))
+        t = _tune_struct(tune)
+        _check(lib.swcorr_plan_batched_tuned(ctypes.byref(h), arr, len(scenes), U16, int(flags),
+                                             ctypes.byref(t) if t is not None else None))
         self._h = h
 
     def run(self, stream=None):
         _check(load().swcorr_run_batched(self._h, _stream_ptr(stream)))
+
+    def tune(self) -> dict:
+        t = TuneStruct()
+        _check(load().swcorr_plan_tune(self._h, ctypes.byref(t)))
+        return _tune_dict(t)
 
     def check_status(self):
         _check(load().swcorr_plan_status(self._h))
