@@ -17,14 +17,13 @@
 //    per output column, updated by the row-pass difference of each new row.
 //  * Step 4: Pearson from the sums (Eq. 2), stored as float32.
 //
-// All sums are kept modulo 2^32, which is exact for sum x and sum y (at most
-// 961 * 65535 < 2^26) and exact for the second-moment sums whenever they are
-// below 2^32.  That is certified by M_w * Sx < 2^32 and M_w * Sy < 2^32,
-// with M_w an upper bound of the window's values (the running maximum of the
-// rows seen in this item): then sum x^2 <= M_w * Sx.  One test on the largest
-// Sx, Sy of a lane's row certifies all its windows at once; a window that
-// fails it (possible only for very bright, wide windows) is tested alone and,
-// if needed, recomputed exactly from shared memory in int64.
+// All sums are kept modulo 2^32, which is exact for sum x and sum y.  Step 4
+// below needs T_x, T_y < 2^32 and |U| < 2^31.  A lane certifies all windows
+// of an output row at once from the range R of the values it has loaded in
+// the item (T <= n (R^2/4 + 5), |U| <= sqrt(T_x T_y)); a row that fails is
+// evaluated per window: certified by M_w * Sx < 2^32 (M_w the running
+// maximum, so sum x^2 <= M_w Sx) and T_x T_y < 2^62, else recomputed exactly
+// in int64 from global memory and counted.
 //
 // Finalize, exact up to the last float32 roundings: with a = an integer near
 // the window mean and r = Sx - n a,
@@ -252,7 +251,8 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     V[c][0] = V[c][1] = 0u;
     VQ[c][0] = VQ[c][1] = VQ[c][2] = (Acc)0;
   }
-  uint32_t mx2 = 0u, my2 = 0u;
+  uint32_t mx2 = 0u, my2 = 0u;             // running maxima (two uint16 per word)
+  uint32_t mn2 = 0xFFFFFFFFu, mny2 = 0xFFFFFFFFu;  // running minima
   int until_out = sc.kh - 1;  // rows until the next output row is complete
   int jr = j0;
 
@@ -307,6 +307,10 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     for (int w = 0; w + 1 < G::NWORD; w += 2) {
       mx2 = __vimax3_u16x2(mx2, we[w], we[w + 1]);
       my2 = __vimax3_u16x2(my2, ye[w], ye[w + 1]);
+      if (!WIDE) {
+        mn2 = __vimin3_u16x2(mn2, we[w], we[w + 1]);
+        mny2 = __vimin3_u16x2(mny2, ye[w], ye[w + 1]);
+      }
     }
 
     // Row pass on the entering-minus-leaving differences, then the running
@@ -390,42 +394,32 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       const uint32_t Mx = max(mx2 & 0xFFFFu, mx2 >> 16), My = max(my2 & 0xFFFFu, my2 >> 16);
       const bool row_interior = (rc - sc.h1 >= 0) && (rc + sc.h2 <= sc.H - 1);
       float* orow = sc.out + (long long)jr * sc.out_pitch;
-      // one certificate for the whole lane row: n Mx^2 < 2^32 bounds every
-      // window's second moment; otherwise its largest sums are tested
-      const uint32_t n_max = (uint32_t)(sc.kh * KW);
-      bool row_cert = (__umulhi(Mx * Mx, n_max) == 0u) && (__umulhi(My * My, n_max) == 0u);
-      if (!row_cert) {
-        uint32_t mSx = V[0][0], mSy = V[0][1];
-#pragma unroll
-        for (int c = 1; c < M; c++) {
-          mSx = max(mSx, V[c][0]);
-          mSy = max(mSy, V[c][1]);
-        }
-        row_cert = certified(Mx, mSx, My, mSy);
-      }
-      bool fast = fast_cols && row_interior && __all_sync(0xffffffffu, row_cert);
+      // One certificate for every window of the lane's row: with R the range
+      // of the values the lane has loaded in this item (its windows' cells
+      // among them), T = sum (x - a)^2 <= n (R^2 / 4 + 5) (Popoviciu's bound
+      // plus (mean - a)^2 < 5) and |U| <= sqrt(T_x T_y); T_x, T_y < 2^32 and
+      // T_x T_y < 2^62 make the 32-bit evaluation exact.
+      const float n_max = (float)(sc.kh * KW);
+      const uint32_t rng_x = Mx - min(mn2 & 0xFFFFu, mn2 >> 16), rng_y = My - min(mny2 & 0xFFFFu, mny2 >> 16);
+      const float bx = n_max * fmaf(0.25f * (float)rng_x, (float)rng_x, 5.0f);
+      const float by = n_max * fmaf(0.25f * (float)rng_y, (float)rng_y, 5.0f);
+      const bool row_cert = bx < 4.2e9f && by < 4.2e9f && bx * by < 4.5e18f;
+      const bool fast = fast_cols && row_interior && __all_sync(0xffffffffu, row_cert);
       if (fast) {
         float res[M];
-        float ttmax = 0.0f;
 #pragma unroll
         for (int c = 0; c < M; c++) {
           float tt;
           res[c] = pearson_u16(V[c][0], V[c][1], (uint32_t)VQ[c][0], (uint32_t)VQ[c][1], (uint32_t)VQ[c][2], n_c[c], fn_c[c],
                                __umulhi(V[c][0], inv_c[c]), __umulhi(V[c][1], inv_c[c]), tt);
-          ttmax = fmaxf(ttmax, tt);
         }
-        // a cross term beyond int32 range (extremely wide, bright windows)
-        // sends the whole row through the per-window path below
-        fast = __all_sync(0xffffffffu, ttmax < TT_LIMIT);
-        if (fast) {
-          if (cl + M <= sc.W) {
+        if (cl + M <= sc.W) {
 #pragma unroll
-            for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
-          } else {
+          for (int c = 0; c < M; c += 4) stg128(orow + cl + c, res[c], res[c + 1], res[c + 2], res[c + 3]);
+        } else {
 #pragma unroll
-            for (int c = 0; c < M; c++)
-              if (cl + c < sc.W) orow[cl + c] = res[c];
-          }
+          for (int c = 0; c < M; c++)
+            if (cl + c < sc.W) orow[cl + c] = res[c];
         }
       }
       if (!fast) {
