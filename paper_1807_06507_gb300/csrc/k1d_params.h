@@ -13,11 +13,11 @@ struct K1DParams {
   int k, h1, h2;     // window and its extents before/after the centre
   int stride;
   long long n_out;   // ceil(N / stride)
-  long long n_items; // chunks
-  int span;          // cells loaded per chunk, rounded up to whole boxes
+  long long n_items; // chunks of (warps per CTA) * 32 * M1 outputs
+  int span;          // cells loaded per chunk (= nbox * 256)
   int nbox;          // TMA boxes per channel per chunk
   int q, r;          // k = q * (M1 * stride) + r
-  int nseg;          // segments of M1*stride cells in the span (<= 64)
+  int nseg;          // segments of M1*stride cells a warp sums (<= 64)
   int is_f32;
   int qbits;         // float32 fixed-point magnitude bits
   const void* gx;    // plain-load fallback (unaligned bases)

@@ -26,7 +26,9 @@ cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
 
 // 1-D (uint16 or float32): outputs per lane per chunk, and the launch.
 int k1d_outputs_per_lane();
-cudaError_t k1d_launch(const K1DParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t k1d_launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st);
+// resident CTAs of `warps` warps per SM with `smem` bytes (0 if the query fails)
+int k1d_blocks_per_sm(bool f32, int warps, size_t smem);
 
 // Batched 2-D uint16: ring row stride, one-time attribute set-up, launch.
 int kbatched_ring_row();

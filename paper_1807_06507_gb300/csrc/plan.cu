@@ -282,6 +282,7 @@ struct swcorr_plan_s {
   size_t smem = 0;
   // 1-D launch
   K1DParams k1{};
+  int warps = 1;  // warps per CTA
   // 3-D launch
   K3DParams k3{};
   Geo3DInfo g3{};
@@ -329,27 +330,43 @@ static swcorr_status plan_1d(swcorr_plan_s* p) {
   k1.h2 = k / 2;
   k1.stride = s;
   k1.n_out = (N + s - 1) / s;
-  k1.n_items = (k1.n_out + L - 1) / L;
   k1.q = (int)q;
   k1.r = (int)(k % seg);
   k1.nseg = (int)std::min<int64_t>(64, 32 + q + 1);
   k1.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
-  const int align = k1.is_f32 ? 4 : 8;
-  const int64_t need = align + (int64_t)(L - 1) * s + k + seg;  // span plus slack for the last segment
-  k1.nbox = (int)((need + 255) / 256);
-  k1.span = k1.nbox * 256;
   if (!k1.is_f32 && (uint64_t)std::min<int64_t>(k, N) > kMaxU16Cells)
     return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows are limited to %llu in-bounds cells (got %d)",
                 (unsigned long long)kMaxU16Cells, k);
   k1.qbits = f32_qbits((uint64_t)k);
-  p->smem = (size_t)2 * k1.span * 4 + (size_t)L * 4 + 16;
+  const int es = k1.is_f32 ? 4 : 2;
+  const int align = 16 / es;
+  // warps per CTA (one chunk of warps * 32 * M1 outputs shares one span):
+  // the most (up to 4, or tile_rows when tuned) whose span fits in 110 KB
+  auto smem_for = [&](int w, int* nbox) -> size_t {
+    const int64_t need = align + (int64_t)(w - 1) * L * s + (int64_t)k1.nseg * seg;  // last warp's segments
+    *nbox = (int)((need + 255) / 256);
+    // (the span, at least w * L cells of two channels, also stages the w * L
+    // float outputs)
+    return (size_t)2 * (*nbox) * 256 * es + 8 + 16 * (size_t)w;
+  };
+  int warps = p->tune.tile_rows > 0 ? std::min(p->tune.tile_rows, 4) : 4;
+  int nbox = 0;
+  while (warps > 1 && smem_for(warps, &nbox) > (size_t)std::min(p->dev.smem_optin, 110 * 1024)) warps--;
+  if ((size_t)2 * nbox * 256 * es < (size_t)warps * L * 4)
+    return fail(SWCORR_ERR_UNSUPPORTED, "1-D span too short to stage the outputs");
+  p->smem = smem_for(warps, &nbox);
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "1-D window %d with stride %d needs %zu B of shared memory", k, s, p->smem);
-  int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (p->smem + 1024))));
+  k1.nbox = nbox;
+  k1.span = nbox * 256;
+  k1.n_items = (k1.n_out + (int64_t)warps * L - 1) / ((int64_t)warps * L);
+  p->warps = warps;
+  int per_sm = k1d_blocks_per_sm(k1.is_f32 != 0, warps, p->smem);
+  if (per_sm < 1) per_sm = 1;
   if (p->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, p->tune.ctas_per_sm);
   p->grid = (int)std::min<int64_t>(k1.n_items, (int64_t)p->dev.sms * per_sm);
   p->tune.prefetch = 1;
-  p->tune.tile_rows = 0;
+  p->tune.tile_rows = warps;
   p->tune.ctas_per_sm = per_sm;
   return SWCORR_OK;
 }
@@ -380,7 +397,7 @@ static swcorr_status run_1d(swcorr_plan_s* p, const void* x, const void* y, floa
   }
   k1.out = c;
   k1.status = p->d_status;
-  cudaError_t e = k1d_launch(k1, p->grid, p->smem, st);
+  cudaError_t e = k1d_launch(k1, p->grid, p->warps, p->smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "1-D kernel launch");
   return SWCORR_OK;
 }
