@@ -50,6 +50,8 @@ struct K3DParams {
   const void* gx;
   const void* gy;
   long long ipy, ipz;  // input pitches (elements) of a row and of a plane
+  int unit_stride;     // sz = sy = sx = 1
+  int vec_store;       // output rows 16-byte aligned (unit strides)
 };
 
 constexpr int K3_THREADS = 128;
@@ -336,7 +338,38 @@ __global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__
       }
 
       // step 4 for the output plane whose window is complete
-      if (s >= p.kz - 1) {
+      if (s >= p.kz - 1 && p.unit_stride) {
+        // unit strides: output (z, y, x) = centre (z, y, x); 4 columns per lane
+        const int zc = zc0 + (s - (p.kz - 1));
+        const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+          const int yc = y0 + warp * 2 + a;
+          if (yc >= p.H) continue;
+          const int cy = min(yc + G::H2, p.H - 1) - max(yc - G::H1, 0) + 1;
+          float* orow = p.out + (long long)zc * p.opz + (long long)yc * p.opy;
+          const int xc0 = x0 + 4 * lane;
+          float res[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const int xc = xc0 + c;
+            const int cx = max(min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1, 0);
+            const uint64_t n = (uint64_t)(uint32_t)(cz * cy) * (uint64_t)cx;
+            const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
+            const long long vx = (long long)(n * V2[a][c] - s0 * s0);
+            const long long vy = (long long)(n * V3[a][c] - s1 * s1);
+            const long long num = (long long)(n * V4[a][c] - s0 * s1);
+            res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+          }
+          if (p.vec_store && xc0 + 3 < p.W) {
+            stg128(orow + xc0, res[0], res[1], res[2], res[3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+              if (xc0 + c < p.W) orow[xc0 + c] = res[c];
+          }
+        }
+      } else if (s >= p.kz - 1) {
         const int zc = zc0 + (s - (p.kz - 1));
         if (zc % p.sz == 0) {
           const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;

@@ -1,11 +1,13 @@
 // kbatched.cu -- one persistent launch over the tiles of many 2-D uint16
 // scenes of uneven sizes and window sizes.
 //
-// Work items (scene, column strip, row block) sit in a device array ordered
-// largest cost first; each CTA (one warp) takes the next item from an atomic
-// counter and runs the fused 2-D kernel body specialised for that scene's
-// window width.  The counter is reset by a memset node in front of the
-// kernel node of the CUDA graph the plan replays on every run.
+// Work items (scene, column strip, row block) sit in device arrays ordered
+// largest cost first, one array per engine (32-bit sums for windows of at
+// most 64 cells and 9 columns, 64-bit otherwise); each CTA (one warp) takes
+// the next item from its array's atomic counter and runs the fused 2-D
+// kernel body specialised for that scene's window width.  The plan replays
+// one CUDA graph: a memset node resetting both counters, then the 32-bit and
+// the 64-bit kernel nodes.
 #include "k2d_u16.cuh"
 #include "launch.h"
 
@@ -17,7 +19,11 @@ __device__ __forceinline__ bool run_item(const Scene2D& sc, int strip, int rb, c
   return process_item_2d_u16<8, KW, true, WIDE>(sc, strip, rb, rg, seq, status);
 }
 
-__global__ void __launch_bounds__(32) kbatched_kernel(const __grid_constant__ KBatchParams p) {
+// One instance per engine: the 32-bit bodies (windows of at most 64 cells and
+// 9 columns) fit 16 resident CTAs per SM; the 64-bit bodies need more
+// registers and run in their own launch.
+template <bool WIDE>
+__global__ void __launch_bounds__(32, WIDE ? 1 : 16) kbatched_kernel(const __grid_constant__ KBatchParams p) {
   constexpr int RWS = Geo2D<8, 31>::RWS;  // the same for every instance with M = 8
   static_assert(Geo2D<8, 3>::RWS == RWS && Geo2D<8, 17>::RWS == RWS, "ring rows differ between instances");
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -44,21 +50,19 @@ __global__ void __launch_bounds__(32) kbatched_kernel(const __grid_constant__ KB
     const BatchItem it = p.items[item];
     const Scene2D sc = p.scenes[it.scene];
     bool ok = true;
-    // 32-bit engine for small windows (kw <= 9, kh*kw <= 64), 64-bit otherwise
-    const int key = sc.wide ? 100 + sc.kw : sc.kw;
-    switch (key) {
-#define X(KW)                                                           \
-  case KW:                                                              \
-    ok = run_item<KW, false>(sc, it.strip, it.rb, rg, seq, p.status);  \
-    break;
-#define XW(KW)                                                          \
-  case 100 + KW:                                                        \
-    ok = run_item<KW, true>(sc, it.strip, it.rb, rg, seq, p.status);   \
+    switch (sc.kw) {
+#define X(KW)                                                    \
+  case KW:                                                       \
+    ok = run_item<KW, WIDE>(sc, it.strip, it.rb, rg, seq, p.status); \
     break;
       X(1) X(3) X(5) X(7) X(9)
-      XW(1) XW(3) XW(5) XW(7) XW(9) XW(11) XW(13) XW(15) XW(17) XW(19) XW(21) XW(23) XW(25) XW(27) XW(29) XW(31)
 #undef X
-#undef XW
+#define X(KW)                                                                \
+  case KW:                                                                   \
+    if constexpr (WIDE) ok = run_item<KW, true>(sc, it.strip, it.rb, rg, seq, p.status); \
+    break;
+      X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31)
+#undef X
       default:
         if (lane == 0) atomicOr(p.status + ST_ERROR, ERRBIT_BAD_ARG);
         ok = false;
@@ -69,14 +73,21 @@ __global__ void __launch_bounds__(32) kbatched_kernel(const __grid_constant__ KB
 
 int kbatched_ring_row() { return Geo2D<8, 31>::RWS; }
 
-const void* kbatched_kernel_ptr() { return reinterpret_cast<const void*>(kbatched_kernel); }
-
-cudaError_t kbatched_prepare() {
-  return cudaFuncSetAttribute(kbatched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+const void* kbatched_kernel_ptr(bool wide) {
+  return wide ? reinterpret_cast<const void*>(kbatched_kernel<true>) : reinterpret_cast<const void*>(kbatched_kernel<false>);
 }
 
-cudaError_t kbatched_launch(const KBatchParams& p, int grid, size_t smem, cudaStream_t st) {
-  kbatched_kernel<<<grid, 32, smem, st>>>(p);
+cudaError_t kbatched_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(kbatched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kbatched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t kbatched_launch(const KBatchParams& p, bool wide, int grid, size_t smem, cudaStream_t st) {
+  if (wide)
+    kbatched_kernel<true><<<grid, 32, smem, st>>>(p);
+  else
+    kbatched_kernel<false><<<grid, 32, smem, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -294,7 +294,8 @@ struct swcorr_plan_s {
   uint32_t* d_status = nullptr;
   // batched plans: device block (scenes, tensor maps, items, counter), graph
   void* d_batch = nullptr;
-  KBatchParams kb{};
+  KBatchParams kbs[2]{};  // 32-bit and 64-bit engine launches
+  int bgrid[2] = {0, 0};
   int64_t batched_outputs = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -495,6 +496,9 @@ static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, cons
   }
   k3.out = c;
   k3.status = p->d_status;
+  k3.unit_stride = (k3.sz == 1 && k3.sy == 1 && k3.sx == 1) ? 1 : 0;
+  k3.vec_store = (k3.unit_stride && (reinterpret_cast<uintptr_t>(c) & 15) == 0 && k3.opy % 4 == 0 && k3.opz % 4 == 0)
+                     ? 1 : 0;
   cudaError_t e = k3d_launch(p->k[2], k3, p->grid, p->smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "3-D kernel launch");
   return SWCORR_OK;
@@ -799,7 +803,7 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
     q.OH = q.H;
     q.OW = q.W;
     q.n_strips = (q.W + 32 * g.M - 1) / (32 * g.M);
-    q.TJ = std::min(q.OH, std::max(rows_min, 4 * q.kh));
+    q.TJ = std::min(q.OH, std::max(rows_min, 2 * q.kh));  // the kh - 1 halo rows re-read stay below half
     q.n_rb = (q.OH + q.TJ - 1) / q.TJ;
     const uint64_t n = (uint64_t)q.kh * (uint64_t)q.kw;
     q.inv_n = n <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / n);
@@ -825,10 +829,17 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   std::vector<int> order(n_scenes);
   for (int i = 0; i < n_scenes; i++) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // 32-bit engine items first, then 64-bit engine items (two launches)
   std::vector<BatchItem> items;
-  for (int i : order)
-    for (int rb = 0; rb < sc[i].n_rb; rb++)
-      for (int strip = 0; strip < sc[i].n_strips; strip++) items.push_back(BatchItem{i, strip, rb, 0});
+  size_t n_narrow = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    for (int i : order) {
+      if (sc[i].wide != pass) continue;
+      for (int rb = 0; rb < sc[i].n_rb; rb++)
+        for (int strip = 0; strip < sc[i].n_strips; strip++) items.push_back(BatchItem{i, strip, rb, 0});
+    }
+    if (pass == 0) n_narrow = items.size();
+  }
   if (items.size() > (size_t)0x7fffffff) return fail(SWCORR_ERR_UNSUPPORTED, "too many work items");
 
   // one device block: maps (64-byte aligned), scenes, items, counter
@@ -867,30 +878,30 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
       (e = cudaMemset(base + ctr_off, 0, 256)) != cudaSuccess ||
       (e = cudaMemset(p->d_status, 0, ST_WORDS * sizeof(uint32_t))) != cudaSuccess)
     return cleanup(cuda_fail(e, "batched plan upload"));
-  KBatchParams& kb = p->kb;
-  kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
-  kb.items = reinterpret_cast<const BatchItem*>(base + it_off);
-  kb.n_items = (int)items.size();
-  kb.PF = tn.prefetch > 0 ? tn.prefetch : 4;
-  kb.NR = kb.PF + 1;
-  kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off);
-  kb.status = p->d_status;
-  p->smem = (size_t)4 * kb.NR * kbatched_ring_row() * 2 + (size_t)kb.NR * 8;
-  int per_sm = 0;
-  p->grid = dev.sms * 8;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(), 32, p->smem) == cudaSuccess &&
-      per_sm > 0)
-    p->grid = dev.sms * per_sm;
-  else
-    per_sm = 8;
-  if (tn.ctas_per_sm > 0 && tn.ctas_per_sm < per_sm) {
-    per_sm = tn.ctas_per_sm;
-    p->grid = dev.sms * per_sm;
+  const int PF = tn.prefetch > 0 ? tn.prefetch : 4;
+  p->smem = (size_t)4 * (PF + 1) * kbatched_ring_row() * 2 + (size_t)(PF + 1) * 8;
+  int per_sm_max = 0;
+  for (int wide = 0; wide < 2; wide++) {
+    KBatchParams& kb = p->kbs[wide];
+    kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
+    kb.items = reinterpret_cast<const BatchItem*>(base + it_off) + (wide ? n_narrow : 0);
+    kb.n_items = (int)(wide ? items.size() - n_narrow : n_narrow);
+    kb.PF = PF;
+    kb.NR = PF + 1;
+    kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off) + wide;
+    kb.status = p->d_status;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(wide != 0), 32, p->smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 8;
+    if (tn.ctas_per_sm > 0) per_sm = std::min(per_sm, tn.ctas_per_sm);
+    p->bgrid[wide] = (int)std::min<int64_t>((int64_t)dev.sms * per_sm, kb.n_items);
+    per_sm_max = std::max(per_sm_max, per_sm);
   }
-  p->grid = (int)std::min<int64_t>(p->grid, kb.n_items);
-  p->tune.prefetch = kb.PF;
+  p->tune.prefetch = PF;
   p->tune.tile_rows = rows_min;
-  p->tune.ctas_per_sm = per_sm;
+  p->tune.ctas_per_sm = per_sm_max;
   *out = p;
   return SWCORR_OK;
 }
@@ -906,8 +917,10 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
       return cuda_fail(e, "create capture stream");
     if ((e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t e1 = cudaMemsetAsync(p->kb.counter, 0, sizeof(uint32_t), p->cap_stream);
-    cudaError_t e2 = kbatched_launch(p->kb, p->grid, p->smem, p->cap_stream);
+    cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, 2 * sizeof(uint32_t), p->cap_stream);
+    cudaError_t e2 = cudaSuccess;
+    for (int wide = 0; wide < 2 && e2 == cudaSuccess; wide++)
+      if (p->kbs[wide].n_items > 0) e2 = kbatched_launch(p->kbs[wide], wide != 0, p->bgrid[wide], p->smem, p->cap_stream);
     e = cudaStreamEndCapture(p->cap_stream, &p->graph);
     if (e1 != cudaSuccess) return cuda_fail(e1, "capture counter reset");
     if (e2 != cudaSuccess) return cuda_fail(e2, "capture batched kernel");
