@@ -32,19 +32,22 @@ def _dev(torch, a):
     return torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda()
 
 
-def _time(torch, fn, reps, warm=3):
+def _time(torch, fn, reps, warm=3, batch=8):
+    """Median over `reps` samples of the per-call time (us) of `batch`
+    back-to-back calls between two CUDA events (launch gaps amortised)."""
     for i in range(warm):
         fn(i)
     torch.cuda.synchronize()
     ts = []
-    for i in range(reps):
+    for r in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        fn(i)
+        for b in range(batch):
+            fn(r * batch + b)
         e1.record()
         torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1) * 1e3)
+        ts.append(e0.elapsed_time(e1) * 1e3 / batch)
     return statistics.median(ts)
 
 
@@ -189,7 +192,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--out", default=swcorr.DEFAULT_TUNE_FILE)
     ap.add_argument("--only", default="", help="comma-separated configuration names")
-    ap.add_argument("--reps", type=int, default=15)
+    ap.add_argument("--reps", type=int, default=7)
     args = ap.parse_args(argv)
     import torch
     swcorr.load()
