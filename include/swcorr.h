@@ -85,7 +85,15 @@ enum {
   /* Also write the five window sums (int64: Sx, Sy, Sxx, Syy, Sxy per output,
    * output-major) to the sums buffer passed to swcorr_run.  uint16 only; the
    * sums are the exact integer sums of Section 1, steps 1-3. */
-  SWCORR_FLAG_EMIT_SUMS = 1u
+  SWCORR_FLAG_EMIT_SUMS = 1u,
+  /* Test hook for the failure path (not part of the paper's method): in a
+   * 2-D uint16 plan whose inputs are read by TMA, the work item of the first
+   * strip and row block announces its first row's copy but never issues it.
+   * That warp's bounded wait gives up after about a second, it drains its
+   * other copies and returns, and swcorr_plan_status reports
+   * SWCORR_ERR_TIMEOUT; every other item completes normally and the context
+   * stays usable.  Outputs of the stalled item are undefined. */
+  SWCORR_FLAG_TEST_STALL = 2u
 };
 
 typedef struct swcorr_plan_s* swcorr_plan;

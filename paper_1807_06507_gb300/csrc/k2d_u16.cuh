@@ -196,6 +196,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
     }
     uint64_t* b = rg.bar + s;
     mbar_arrive_expect_tx(b, (lv ? 2u : 1u) * 2u * G::RW * 2u);
+    if (sc.test_stall && strip == 0 && rb == 0 && i == 0) return;  // the failure-path test hook
     auto row_boxes = [&](uint16_t* dx, uint16_t* dy, int r) {
 #pragma unroll
       for (int q = 0; q < G::NMAIN; q++) {

@@ -40,6 +40,7 @@ struct Scene2D {
   long long* sums;         // optional 5 int64 per output (debug / bit-exact tests)
   int qbits;               // float32 path: fixed-point magnitude bits (|X| < 2^qbits)
   int wide;                // uint16 path: 64-bit second-moment sums (large windows)
+  int test_stall;          // test hook: item (0, 0) never issues its first row's copy
 };
 
 struct K2DParams {

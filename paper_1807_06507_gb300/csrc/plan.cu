@@ -505,8 +505,10 @@ static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, cons
 }
 
 static swcorr_status plan_2d(swcorr_plan_s* p) {
-  return setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1], p->stride[0],
-                  p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid, &p->tune);
+  swcorr_status st = setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1],
+                              p->stride[0], p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid, &p->tune);
+  p->k2.sc.test_stall = (p->flags & SWCORR_FLAG_TEST_STALL) ? 1 : 0;
+  return st;
 }
 
 extern "C" {
@@ -550,7 +552,10 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   if (!shape || !k) return fail(SWCORR_ERR_INVALID_ARG, "shape and k must not be NULL");
   if (dtype != SWCORR_U16 && dtype != SWCORR_F32) return fail(SWCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
   if (border != SWCORR_BORDER_CLIP) return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
-  if (flags & ~(uint32_t)SWCORR_FLAG_EMIT_SUMS) return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
+  if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL))
+    return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
+  if ((flags & SWCORR_FLAG_TEST_STALL) && !(ndim == 2 && dtype == SWCORR_U16))
+    return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_TEST_STALL applies to 2-D uint16 plans");
   if ((flags & SWCORR_FLAG_EMIT_SUMS) && dtype != SWCORR_U16)
     return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_EMIT_SUMS needs uint16 data");
   swcorr_plan_s tmp;

@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_CUDA, ERR_OOM, ERR_TIME
 U16, F32 = 1, 2
 BORDER_CLIP = 0
 FLAG_EMIT_SUMS = 1
+FLAG_TEST_STALL = 2
 
 EXPORTS = ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune", "swcorr_set_tune_file",
            "swcorr_tune_lookup", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",

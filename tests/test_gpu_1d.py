@@ -36,6 +36,7 @@ def test_random_walk_f32(sw, n, k):
 
 
 @pytest.mark.parametrize("n,k,stride", [(40_000, 101, 1), (40_000, 101, 3), (5_555, 64, 2), (777, 1001, 1),
+                                        (70_000, 2015, 1), (33_333, 4000, 5), (20_000, 31, 9),
                                         (1, 5, 1), (2, 1, 1), (100, 100, 7)])
 def test_u16_series_exact_nan(sw, n, k, stride):
     rng = np.random.default_rng(n + k)
@@ -83,3 +84,12 @@ def test_unaligned_base_plain_loads(sw):
     torch.cuda.synchronize()
     ref, rx, ry = oracle.corr(buf_x[1:].copy(), buf_y[1:].copy(), 51, relvar=True)
     score(c.cpu().numpy(), ref, rx, ry, exact_nan=False)
+
+
+@pytest.mark.parametrize("n,k,stride", [(30_000, 301, 2), (50_000, 1001, 1), (9_000, 2015, 1), (12_345, 500, 7)])
+def test_f32_strides_and_chunk_seams(sw, n, k, stride):
+    # chunks of 4 warps x 2016 outputs: seams between warps and between chunks
+    x, y = W.random_walk_pair(n, seed=n + 3 * k, flip=1500)
+    c = run1(sw, x, y, k, stride)
+    ref, rx, ry = oracle.corr(x, y, k, stride, relvar=True)
+    score(c, ref, rx, ry, exact_nan=False)

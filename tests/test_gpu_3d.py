@@ -36,7 +36,8 @@ def test_halfspace_volume_small(sw, stride):
 
 
 @pytest.mark.parametrize("shape,k", [((12, 33, 260), (3, 5, 5)), ((9, 20, 140), (5, 3, 3)), ((1, 1, 1), 3),
-                                     ((5, 3, 200), 7), ((17, 9, 129), (1, 1, 1)), ((6, 30, 64), (9, 15, 15))])
+                                     ((5, 3, 200), 7), ((17, 9, 129), (1, 1, 1)), ((6, 30, 64), (9, 15, 15)),
+                                     ((7, 11, 131), (3, 5, 5)), ((40, 17, 250), (15, 3, 3))])
 def test_u16_volumes_exact(sw, shape, k):
     rng = np.random.default_rng(sum(shape))
     x = rng.integers(0, 65536, shape).astype(np.uint16)

@@ -57,3 +57,27 @@ def test_batched_rejects_unaligned_pitch():
     with pytest.raises(swcorr.SwcorrError) as ei:
         swcorr.BatchedPlan([(x, x, c, 3)])
     assert ei.value.status == swcorr.ERR_ALIGNMENT
+
+
+@pytest.mark.parametrize("ks", [(3, 5, 7), (15, 31), ((3, 9), (9, 3), 1)])
+def test_batched_single_engine_and_rectangular(ks):
+    # only the 32-bit engine, only the 64-bit engine, rectangular windows
+    from paper_1807_06507_gb300 import swcorr
+    swcorr.load()
+    rng = np.random.default_rng(len(ks))
+    dev, ref = [], []
+    for i, k in enumerate(ks):
+        h, w = int(rng.integers(40, 300)), int(rng.integers(30, 700))
+        x, y = W.night_scene((h, w), seed=100 + i)
+        xd = to_dev(padded(x), torch)[:, :w]
+        yd = to_dev(padded(y), torch)[:, :w]
+        c = torch.full((h, w), -5.0, dtype=torch.float32, device="cuda")
+        dev.append((xd, yd, c, k))
+        ref.append(oracle.corr(x, y, k))
+    bp = swcorr.BatchedPlan(dev)
+    bp.run()
+    torch.cuda.synchronize()
+    bp.check_status()
+    for (_, _, c, _), r in zip(dev, ref):
+        score(c.cpu().numpy(), r)
+    bp.close()
