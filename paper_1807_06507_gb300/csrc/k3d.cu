@@ -57,4 +57,23 @@ cudaError_t k3d_launch(int k, const K3DParams& p, int grid, size_t smem, cudaStr
   }
 }
 
+int k3d_blocks_per_sm(int k, size_t smem) {
+  int b = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (k) {
+#define X(K)                                                                                        \
+  case K:                                                                                           \
+    e = cudaFuncSetAttribute(k3d_kernel<kTY3, kTX3, K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             200 * 1024);                                                           \
+    if (e == cudaSuccess)                                                                           \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k3d_kernel<kTY3, kTX3, K, K>, K3_THREADS, smem); \
+    break;
+    SWC_K3D_CASES(X)
+#undef X
+    default:
+      break;
+  }
+  return e == cudaSuccess ? b : 0;
+}
+
 }  // namespace swc

@@ -70,7 +70,7 @@ struct Geo3D {
 };
 
 template <int TY, int TX, int KY, int KX>
-__global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__ K3DParams p) {
+__global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constant__ K3DParams p) {
   using G = Geo3D<TY, TX, KY, KX>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int esz = p.is_f32 ? 4 : 2;
@@ -78,10 +78,11 @@ __global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__
   const size_t plane_stride = (plane_bytes + 127) / 128 * 128;  // TMA destinations are 128-byte aligned
   const size_t slot_bytes = 2 * plane_stride;                   // x, then y
   const int yoff = (int)(plane_stride / esz);                    // y channel, in elements
-  // slots: [0,1] entering, [2,3] leaving
+  // slots: 0 entering plane, 1 leaving plane (the range pass of float32
+  // items alternates between both)
   unsigned char* slots = smem_raw;
-  uint32_t* VS = reinterpret_cast<uint32_t*>(smem_raw + 4 * slot_bytes);  // [8][TY][VSP]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(VS + 8 * TY * G::VSP);      // 4 mbarriers
+  uint32_t* VS = reinterpret_cast<uint32_t*>(smem_raw + 2 * slot_bytes);  // [8][TY][VSP]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(VS + 8 * TY * G::VSP);      // 2 mbarriers (4 reserved)
   __shared__ float red[4][K3_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -216,30 +217,27 @@ __global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__
         V0[a][c] = V1[a][c] = 0u;
         V2[a][c] = V3[a][c] = V4[a][c] = 0ull;
       }
-    // entering plane of step s in slot s&1, leaving plane (step s >= kz) in
-    // slot 2 + (s&1); both are requested one step ahead
+    // entering plane of step s in slot 0, leaving plane (step s >= kz) in
+    // slot 1; the copies of step s + 1 are issued as soon as the vertical
+    // pass of step s has read both, so they overlap the horizontal pass
     if (tid == 0 && p.use_tma) {
       fence_proxy_async_smem();
-      issue(0, ze0);
+      issue(0, ze0);  // kz >= 1: no leaving plane at step 0
     }
     for (int s = 0; s < nsteps; s++) {
       const int ze = ze0 + s, zl = ze - p.kz;
       const bool has_leave = s >= p.kz;
       if (!p.use_tma) {
-        load_plain(s & 1, ze);
-        if (has_leave) load_plain(2 + (s & 1), zl);
+        load_plain(0, ze);
+        if (has_leave) load_plain(1, zl);
         __syncthreads();
-      } else if (tid == 0 && s + 1 < nsteps) {
-        fence_proxy_async_smem();
-        issue((s + 1) & 1, ze + 1);
-        if (s + 1 >= p.kz) issue(2 + ((s + 1) & 1), ze + 1 - p.kz);
       }
-      if (!wait_slot(s & 1)) return;
-      if (has_leave && !wait_slot(2 + (s & 1))) return;
+      if (!wait_slot(0)) return;
+      if (has_leave && !wait_slot(1)) return;
       const bool ze_ok = ze >= 0 && ze < p.Z;
       const bool zl_ok = has_leave && zl >= 0 && zl < p.Z;
-      const unsigned char* se = slots + (s & 1) * slot_bytes;
-      const unsigned char* sl = slots + (2 + (s & 1)) * slot_bytes;
+      const unsigned char* se = slots;
+      const unsigned char* sl = slots + slot_bytes;
 
       // vertical pass: thread per input column
       for (int c = tid; c < G::TXI; c += K3_THREADS) {
@@ -305,6 +303,12 @@ __global__ void __launch_bounds__(K3_THREADS) k3d_kernel(const __grid_constant__
         (void)fsl_y;
       }
       __syncthreads();
+      // both slots are free: request step s + 1
+      if (tid == 0 && p.use_tma && s + 1 < nsteps) {
+        fence_proxy_async_smem();
+        issue(0, ze + 1);
+        if (s + 1 >= p.kz) issue(1, ze + 1 - p.kz);
+      }
 
       // horizontal pass: warp -> 2 output rows, lane -> 4 output columns
 #pragma unroll

@@ -433,10 +433,11 @@ static swcorr_status plan_3d(swcorr_plan_s* p) {
                 (unsigned long long)kMaxU16Cells);
   const int eb = k3.is_f32 ? 4 : 2;
   const size_t slot = 2 * (((size_t)g.TYI * g.BXW * eb + 127) / 128 * 128);
-  p->smem = 4 * slot + (size_t)8 * g.TY * g.VSP * 4 + 32;
+  p->smem = 2 * slot + (size_t)8 * g.TY * g.VSP * 4 + 32;  // entering and leaving slot, vertical sums, barriers
   if (p->smem > (size_t)p->dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "3-D plan needs %zu B of shared memory", p->smem);
-  int per_sm = std::max(1, std::min(4, (int)((220 * 1024) / (p->smem + 2048))));
+  int per_sm = k3d_blocks_per_sm(p->k[2], p->smem);
+  if (per_sm < 1) per_sm = 1;
   if (p->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, p->tune.ctas_per_sm);
   const int slots = p->dev.sms * per_sm;
   const int planes_min = p->tune.tile_rows > 0 ? p->tune.tile_rows : 16;
