@@ -6,7 +6,7 @@
 namespace swc {
 
 template <int M, int KW, bool TMA>
-__global__ void __launch_bounds__(32) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
+__global__ void __launch_bounds__(32, 12) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
   using G = Geo2DF<M, KW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring2DF rg;
@@ -14,7 +14,9 @@ __global__ void __launch_bounds__(32) k2d_f32_kernel(const __grid_constant__ K2D
   rg.PF = p.PF;
   rg.rx = reinterpret_cast<float*>(smem_raw);
   rg.ry = rg.rx + (size_t)p.NR * G::RWS;
-  rg.bar = reinterpret_cast<uint64_t*>(rg.ry + (size_t)p.NR * G::RWS);
+  rg.lx = rg.ry + (size_t)p.NR * G::RWS;
+  rg.ly = rg.lx + (size_t)p.NR * G::RWS;
+  rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
     fence_mbar_init();

@@ -53,8 +53,10 @@ struct Geo2DF {
 };
 
 struct Ring2DF {
-  float* rx;      // [NR][RWS]
-  float* ry;      // [NR][RWS]
+  float* rx;      // entering rows [NR][RWS]
+  float* ry;
+  float* lx;      // leaving rows (pass 2) [NR][RWS]
+  float* ly;
   uint64_t* bar;  // [NR]
   int NR;
   int PF;
@@ -101,35 +103,45 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   const uint32_t NR = (uint32_t)rg.NR;
   const int PF = rg.PF;
 
-  auto issue = [&](uint32_t s, int row) {
+  // row `row` into slot s (entering part) and, when lrow is on the item's
+  // leaving side (pass 2, i >= kh), row lrow into the leaving part
+  auto issue = [&](uint32_t s, int row, bool with_leave, int lrow) {
     if (!TMA) {
-      const bool row_ok = row >= 0 && row < sc.H;
-      const float* gx = (const float*)sc.gx + (long long)(row_ok ? row : 0) * sc.in_pitch;
-      const float* gy = (const float*)sc.gy + (long long)(row_ok ? row : 0) * sc.in_pitch;
-      for (int e = lane; e < G::RW; e += 32) {
-        const int col = xs + e;
-        const bool ok = row_ok && col >= 0 && col < sc.W;
-        rg.rx[(size_t)s * G::RWS + e] = ok ? __ldg(gx + col) : 0.0f;
-        rg.ry[(size_t)s * G::RWS + e] = ok ? __ldg(gy + col) : 0.0f;
-      }
+      auto copy_row = [&](float* dx, float* dy, int r) {
+        const bool row_ok = r >= 0 && r < sc.H;
+        const float* gx = (const float*)sc.gx + (long long)(row_ok ? r : 0) * sc.in_pitch;
+        const float* gy = (const float*)sc.gy + (long long)(row_ok ? r : 0) * sc.in_pitch;
+        for (int e = lane; e < G::RW; e += 32) {
+          const int col = xs + e;
+          const bool ok = row_ok && col >= 0 && col < sc.W;
+          dx[e] = ok ? __ldg(gx + col) : 0.0f;
+          dy[e] = ok ? __ldg(gy + col) : 0.0f;
+        }
+      };
+      copy_row(rg.rx + (size_t)s * G::RWS, rg.ry + (size_t)s * G::RWS, row);
+      if (with_leave) copy_row(rg.lx + (size_t)s * G::RWS, rg.ly + (size_t)s * G::RWS, lrow);
       return;
     }
     uint64_t* b = rg.bar + s;
-    mbar_arrive_expect_tx(b, 2u * G::RW * 4u);
+    mbar_arrive_expect_tx(b, (with_leave ? 2u : 1u) * 2u * G::RW * 4u);
+    auto row_boxes = [&](float* dx, float* dy, int r) {
 #pragma unroll
-    for (int q = 0; q < G::NMAIN; q++) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + q * 256, sc.tmx, xs + q * 256, row, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + q * 256, sc.tmy, xs + q * 256, row, b);
-    }
-    if (G::TAIL > 0) {
-      tma_load_2d(rg.rx + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, row, b);
-      tma_load_2d(rg.ry + (size_t)s * G::RWS + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, row, b);
-    }
+      for (int q = 0; q < G::NMAIN; q++) {
+        tma_load_2d(dx + q * 256, sc.tmx, xs + q * 256, r, b);
+        tma_load_2d(dy + q * 256, sc.tmy, xs + q * 256, r, b);
+      }
+      if (G::TAIL > 0) {
+        tma_load_2d(dx + G::NMAIN * 256, sc.tmx_t, xs + G::NMAIN * 256, r, b);
+        tma_load_2d(dy + G::NMAIN * 256, sc.tmy_t, xs + G::NMAIN * 256, r, b);
+      }
+    };
+    row_boxes(rg.rx + (size_t)s * G::RWS, rg.ry + (size_t)s * G::RWS, row);
+    if (with_leave) row_boxes(rg.lx + (size_t)s * G::RWS, rg.ly + (size_t)s * G::RWS, lrow);
   };
 
   // One streaming pass over the item's rows through the ring: issue ahead,
   // wait, hand the slot to body(i, slot), keep the ring bookkeeping.
-  auto stream_rows = [&](auto&& body) -> bool {
+  auto stream_rows = [&](bool leaving, auto&& body) -> bool {
     uint32_t s = seq % NR, lap = (seq / NR) & 1u, sp = (s + (uint32_t)PF) % NR;
     {
       const int npre = min(PF, nrows);
@@ -137,7 +149,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         if (TMA) fence_proxy_async_smem();
         uint32_t si = s;
         for (int i = 0; i < npre; i++) {
-          issue(si, t0 + i);
+          issue(si, t0 + i, leaving && i >= sc.kh, t0 + i - sc.kh);
           si = (si + 1 == NR) ? 0u : si + 1;
         }
       }
@@ -146,7 +158,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
       __syncwarp();
       if (i + PF < nrows && (!TMA || lane == 0)) {
         if (TMA) fence_proxy_async_smem();
-        issue(sp, t0 + i + PF);
+        issue(sp, t0 + i + PF, leaving && i + PF >= sc.kh, t0 + i + PF - sc.kh);
       }
       sp = (sp + 1 == NR) ? 0u : sp + 1;
       if (!TMA) {
@@ -178,7 +190,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
-  if (!stream_rows([&](int i, uint32_t s) {
+  if (!stream_rows(false, [&](int i, uint32_t s) {
         if (t0 + i < 0 || t0 + i >= sc.H) return;
         const float* px = lane_ptr(rg.rx, s);
         const float* py = lane_ptr(rg.ry, s);
@@ -226,13 +238,12 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   const uint32_t seq0 = seq;
 
   // ---- pass 2: the D-march on fixed-point values
-  const bool ok = stream_rows([&](int i, uint32_t s) {
+  const bool ok = stream_rows(true, [&](int i, uint32_t s) {
     const bool has_leave = i >= sc.kh;
-    const uint32_t sl = (uint32_t)(((int)s - sc.kh % (int)NR + (int)NR) % (int)NR);
     const float* pxe = lane_ptr(rg.rx, s);
     const float* pye = lane_ptr(rg.ry, s);
-    const float* pxl = lane_ptr(rg.rx, sl);
-    const float* pyl = lane_ptr(rg.ry, sl);
+    const float* pxl = lane_ptr(rg.lx, s);
+    const float* pyl = lane_ptr(rg.ly, s);
     const int te = t0 + i, tl = te - sc.kh;
     const bool e_ok = te >= 0 && te < sc.H;
     const bool l_ok = has_leave && tl >= 0 && tl < sc.H;

@@ -184,13 +184,12 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
   // uint16 windows with more than 64 cells routinely have second moments
   // beyond 2^32: use the 64-bit engine there
   sc.wide = (!f32 && n > 64) ? 1 : 0;
-  // uint16: rings of entering and leaving rows, PF + 1 slots each; float32:
-  // one ring holding the column window plus the prefetch
+  // rings of entering and leaving rows (x and y), PF + 1 slots each
   const int PF = tune->prefetch > 0 ? tune->prefetch : (f32 ? 3 : 4);
-  const int NR = f32 ? kh + 1 + PF : PF + 1;
+  const int NR = PF + 1;
   k2->NR = NR;
   k2->PF = PF;
-  const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 2 * (f32 ? 1 : 2) + (size_t)NR * 8;
+  const size_t smem = (size_t)NR * g.RWS * (f32 ? 4 : 2) * 4 + (size_t)NR * 8;
   if (smem > (size_t)dev.smem_optin)
     return fail(SWCORR_ERR_UNSUPPORTED, "window height %d needs %zu B of shared memory", kh, smem);
   int per_sm = std::max(1, std::min(16, (int)((200 * 1024) / (smem + 1024))));
