@@ -64,20 +64,20 @@ CONFIGS = {
     "2d_u16_k5": ("plain", "u16", (3000, 4000), (5, 5), None,
                   dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 20, 28, 40, 56], ctas_per_sm=[0, 12])),
     "2d_u16_k7": ("plain", "u16", (3000, 4000), (7, 7), None,
-                  dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 21, 28, 40, 56], ctas_per_sm=[0, 12])),
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[14, 16, 21, 28, 40], ctas_per_sm=[0, 12, 14])),
     "2d_u16_k9": ("plain", "u16", (3000, 4000), (9, 9), None,
-                  dict(prefetch=[2, 3, 4, 6], tile_rows=[24, 36, 48, 64], ctas_per_sm=[0])),
+                  dict(prefetch=[2, 3, 4, 6], tile_rows=[12, 18, 24, 36], ctas_per_sm=[0, 10])),
     "2d_u16_k15": ("plain", "u16", (3000, 4000), (15, 15), None,
-                   dict(prefetch=[2, 3, 4, 6], tile_rows=[30, 45, 60, 90], ctas_per_sm=[0])),
+                   dict(prefetch=[2, 3, 4, 6], tile_rows=[20, 30, 45, 60], ctas_per_sm=[0, 10])),
     "2d_u16_k31": ("plain", "u16", (3000, 4000), (31, 31), None,
-                   dict(prefetch=[2, 3, 4, 6], tile_rows=[62, 93, 124, 186], ctas_per_sm=[0])),
+                   dict(prefetch=[2, 3, 4, 6], tile_rows=[40, 62, 93, 124], ctas_per_sm=[0])),
     "2d_f32_k7": ("plain", "f32", (3000, 4000), (7, 7), None,
                   dict(prefetch=[2, 3, 4], tile_rows=[16, 21, 28, 40], ctas_per_sm=[0, 8, 10])),
     "1d_f32_k1001": ("plain", "f32", (1 << 26,), (1001,), None, dict(ctas_per_sm=[2, 3, 4, 5, 6, 8, 0])),
     "3d_f32_k9": ("plain", "f32", (256, 512, 512), (9, 9, 9), None,
                   dict(tile_rows=[8, 16, 32], ctas_per_sm=[1, 2, 3, 4])),
     "batched_u16": ("batched", "u16", None, None, None,
-                    dict(prefetch=[3, 4, 6], tile_rows=[32, 64, 128])),
+                    dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 32, 64, 128])),
 }
 
 

@@ -32,9 +32,10 @@ int k1d_blocks_per_sm(bool f32, int warps, size_t smem);
 
 // Batched 2-D uint16: ring row stride, one-time attribute set-up, launch.
 int kbatched_ring_row();
-const void* kbatched_kernel_ptr(bool wide);
+// Batched kernel classes: 0 = 32-bit engine, 1 = 64-bit up to 17 columns, 2 = 64-bit above.
+const void* kbatched_kernel_ptr(int cls);
 cudaError_t kbatched_prepare();
-cudaError_t kbatched_launch(const KBatchParams& p, bool wide, int grid, size_t smem, cudaStream_t st);
+cudaError_t kbatched_launch(const KBatchParams& p, int cls, int grid, size_t smem, cudaStream_t st);
 
 // 3-D (uint16 or float32), square in-plane windows ky = kx = k.
 struct Geo3DInfo {

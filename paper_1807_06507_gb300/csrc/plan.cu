@@ -200,8 +200,8 @@ swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int
   if (tune->ctas_per_sm > 0) per_sm = std::min(per_sm, tune->ctas_per_sm);
   const int total = dev.sms * per_sm;
   // one wave of work items over the resident warps, but tiles at least
-  // tile_rows tall (default 4 kh rows: the halo re-read stays below 25 %)
-  const int rows_min = tune->tile_rows > 0 ? tune->tile_rows : std::max(16, 4 * kh / std::max(1, sc.sy));
+  // tile_rows tall (default 2 kh rows: the halo re-read stays below half)
+  const int rows_min = tune->tile_rows > 0 ? tune->tile_rows : std::max(16, 2 * kh / std::max(1, sc.sy));
   int TJ = (int)((sc.OH * (int64_t)sc.n_strips + total - 1) / total);
   TJ = std::max(TJ, rows_min);
   TJ = std::min(TJ, sc.OH);
@@ -293,8 +293,8 @@ struct swcorr_plan_s {
   uint32_t* d_status = nullptr;
   // batched plans: device block (scenes, tensor maps, items, counter), graph
   void* d_batch = nullptr;
-  KBatchParams kbs[2]{};  // 32-bit and 64-bit engine launches
-  int bgrid[2] = {0, 0};
+  KBatchParams kbs[3]{};  // launches per kernel class (32-bit; 64-bit <= 17 columns; 64-bit wider)
+  int bgrid[3] = {0, 0, 0};
   int64_t batched_outputs = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -834,17 +834,20 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   std::vector<int> order(n_scenes);
   for (int i = 0; i < n_scenes; i++) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  // 32-bit engine items first, then 64-bit engine items (two launches)
+  // items grouped by kernel class (32-bit engine; 64-bit up to 17 columns;
+  // 64-bit above), one launch each
+  auto cls_of = [&](int i) { return sc[i].wide == 0 ? 0 : (sc[i].kw <= 17 ? 1 : 2); };
   std::vector<BatchItem> items;
-  size_t n_narrow = 0;
-  for (int pass = 0; pass < 2; pass++) {
+  size_t cls_start[4] = {0, 0, 0, 0};
+  for (int cls = 0; cls < 3; cls++) {
+    cls_start[cls] = items.size();
     for (int i : order) {
-      if (sc[i].wide != pass) continue;
+      if (cls_of(i) != cls) continue;
       for (int rb = 0; rb < sc[i].n_rb; rb++)
         for (int strip = 0; strip < sc[i].n_strips; strip++) items.push_back(BatchItem{i, strip, rb, 0});
     }
-    if (pass == 0) n_narrow = items.size();
   }
+  cls_start[3] = items.size();
   if (items.size() > (size_t)0x7fffffff) return fail(SWCORR_ERR_UNSUPPORTED, "too many work items");
 
   // one device block: maps (64-byte aligned), scenes, items, counter
@@ -886,22 +889,21 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   const int PF = tn.prefetch > 0 ? tn.prefetch : 4;
   p->smem = (size_t)4 * (PF + 1) * kbatched_ring_row() * 2 + (size_t)(PF + 1) * 8;
   int per_sm_max = 0;
-  for (int wide = 0; wide < 2; wide++) {
-    KBatchParams& kb = p->kbs[wide];
+  for (int cls = 0; cls < 3; cls++) {
+    KBatchParams& kb = p->kbs[cls];
     kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
-    kb.items = reinterpret_cast<const BatchItem*>(base + it_off) + (wide ? n_narrow : 0);
-    kb.n_items = (int)(wide ? items.size() - n_narrow : n_narrow);
+    kb.items = reinterpret_cast<const BatchItem*>(base + it_off) + cls_start[cls];
+    kb.n_items = (int)(cls_start[cls + 1] - cls_start[cls]);
     kb.PF = PF;
     kb.NR = PF + 1;
-    kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off) + wide;
+    kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off) + cls;
     kb.status = p->d_status;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(wide != 0), 32, p->smem) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(cls), 32, p->smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 8;
     if (tn.ctas_per_sm > 0) per_sm = std::min(per_sm, tn.ctas_per_sm);
-    p->bgrid[wide] = (int)std::min<int64_t>((int64_t)dev.sms * per_sm, kb.n_items);
+    p->bgrid[cls] = (int)std::min<int64_t>((int64_t)dev.sms * per_sm, kb.n_items);
     per_sm_max = std::max(per_sm_max, per_sm);
   }
   p->tune.prefetch = PF;
@@ -922,10 +924,10 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
       return cuda_fail(e, "create capture stream");
     if ((e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, 2 * sizeof(uint32_t), p->cap_stream);
+    cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, 3 * sizeof(uint32_t), p->cap_stream);
     cudaError_t e2 = cudaSuccess;
-    for (int wide = 0; wide < 2 && e2 == cudaSuccess; wide++)
-      if (p->kbs[wide].n_items > 0) e2 = kbatched_launch(p->kbs[wide], wide != 0, p->bgrid[wide], p->smem, p->cap_stream);
+    for (int cls = 0; cls < 3 && e2 == cudaSuccess; cls++)
+      if (p->kbs[cls].n_items > 0) e2 = kbatched_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream);
     e = cudaStreamEndCapture(p->cap_stream, &p->graph);
     if (e1 != cudaSuccess) return cuda_fail(e1, "capture counter reset");
     if (e2 != cudaSuccess) return cuda_fail(e2, "capture batched kernel");
