@@ -8,29 +8,37 @@ constexpr int kM1 = 63;  // outputs per lane per chunk (odd: conflict-free strid
 
 int k1d_outputs_per_lane() { return kM1; }
 
-template <bool F32>
+template <bool F32, bool UNIT>
 static cudaError_t launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k1d_kernel<kM1, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(k1d_kernel<kM1, F32, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  k1d_kernel<kM1, F32><<<grid, 32 * warps, smem, st>>>(p);
+  k1d_kernel<kM1, F32, UNIT><<<grid, 32 * warps, smem, st>>>(p);
   return cudaGetLastError();
 }
 
+// Separate instances for unit stride and any stride keep each kernel's fully
+// unrolled slide loop alone in the instruction cache.
 cudaError_t k1d_launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st) {
-  return p.is_f32 ? launch<true>(p, grid, warps, smem, st) : launch<false>(p, grid, warps, smem, st);
+  if (p.stride == 1)
+    return p.is_f32 ? launch<true, true>(p, grid, warps, smem, st) : launch<false, true>(p, grid, warps, smem, st);
+  return p.is_f32 ? launch<true, false>(p, grid, warps, smem, st) : launch<false, false>(p, grid, warps, smem, st);
 }
 
 int k1d_blocks_per_sm(bool f32, int warps, size_t smem) {
+  // the unit-stride and any-stride instances share launch bounds and layout
   int b = 0;
-  cudaError_t e = f32 ? cudaFuncSetAttribute(k1d_kernel<kM1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024)
-                      : cudaFuncSetAttribute(k1d_kernel<kM1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = f32 ? cudaFuncSetAttribute(k1d_kernel<kM1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024)
+                      : cudaFuncSetAttribute(k1d_kernel<kM1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
   if (e != cudaSuccess) return 0;
-  e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, true>, 32 * warps, smem)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, false>, 32 * warps, smem);
+  e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, true, true>, 32 * warps, smem)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, false, true>, 32 * warps, smem);
   return e == cudaSuccess ? b : 0;
 }
 

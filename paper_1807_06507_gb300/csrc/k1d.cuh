@@ -119,7 +119,7 @@ __device__ __forceinline__ int to_fixed(float v, float m, float s) {
   return __float_as_int(fmaf(v - m, s, 12582912.0f)) - 0x4B400000;
 }
 
-template <int M1, bool F32>
+template <int M1, bool F32, bool UNIT>
 __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1DParams p) {
   constexpr int LW = 32 * M1;  // outputs per warp
   static_assert(LW % 4 == 0, "vector stores of the staged outputs");
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
   }
   __syncthreads();
   uint32_t phase = 0;
-  const int seg = M1 * p.stride;
+  const int seg = M1 * (UNIT ? 1 : p.stride);
   const int ncell = p.nbox * 256;
 
   for (long long item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     const int e_out = woff + lane * seg;  // first cell of the lane's first window
     const int e_in = e_out + p.k;         // first cell to enter after it
     float res[M1];
-    if (p.stride == 1) {
+    if constexpr (UNIT) {  // stride 1
 #pragma unroll
       for (int t = 0; t < M1; t++) {
         res[t] = pearson_exact(W, n_of(j_base + t));
