@@ -37,8 +37,9 @@ __global__ void __launch_bounds__(32, 12) k2d_f32_kernel(const __grid_constant__
   sc.tmy_t = &p.tmy_t;
   uint32_t seq = 0;
   for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-    const int rb = item / sc.n_strips;
-    const int strip = item - rb * sc.n_strips;
+    const int rbi = item / sc.n_strips;
+    const int strip = item - rbi * sc.n_strips;
+    const int rb = p.rb0 + rbi;
     if (!process_item_2d_f32<M, KW, TMA>(sc, strip, rb, rg, seq, p.status)) return;
   }
 }

@@ -498,8 +498,9 @@ __global__ void __launch_bounds__(32, WIDE ? (KW <= 17 ? 12 : 8) : 1) k2d_u16_ke
   sc.tmy_t = &p.tmy_t;
   uint32_t seq = 0;
   for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-    const int rb = item / sc.n_strips;
-    const int strip = item - rb * sc.n_strips;
+    const int rbi = item / sc.n_strips;
+    const int strip = item - rbi * sc.n_strips;
+    const int rb = p.rb0 + rbi;
     if (!process_item_2d_u16<M, KW, TMA, WIDE>(sc, strip, rb, rg, seq, p.status)) return;
   }
 }

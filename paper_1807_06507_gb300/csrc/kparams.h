@@ -49,7 +49,8 @@ struct K2DParams {
   CUtensorMap tmx_t;
   CUtensorMap tmy_t;
   Scene2D sc;
-  int n_items;
+  int n_items;      // work items of this launch: row blocks [rb0, rb0 + n_items / n_strips) x strips
+  int rb0;          // first row block (0 unless a launch covers one band of the output)
   int NR;           // ring rows
   int PF;           // rows prefetched ahead
   uint32_t* status;

@@ -303,6 +303,12 @@ struct swcorr_plan_s {
   void* d_x = nullptr;
   void* d_y = nullptr;
   float* d_c = nullptr;
+  // banded host runs of 2-D plans: input copies, band kernels, output copies
+  static constexpr int kBands = 8;
+  cudaStream_t hs_in = nullptr, hs_out = nullptr;
+  cudaStream_t hs_k[kBands] = {};
+  cudaEvent_t he_start = nullptr;
+  cudaEvent_t he_in[kBands] = {}, he_k[kBands] = {};
 };
 
 static int64_t n_outputs(const swcorr_plan_s* p) {
@@ -671,6 +677,87 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);
 }
 
+// Host run of a 2-D plan, pipelined over bands of row blocks: the input rows
+// a band needs (its rows plus the window halo) are copied in order on one
+// stream; each band's kernel launch waits only for its own input and runs on
+// its own stream, so band kernels overlap each other and the copies; each
+// band's output rows go back as soon as its kernel ends.  Synchronous, like
+// swcorr_run_host.
+static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const void* y, float* c, cudaStream_t st) {
+  cudaError_t e;
+  constexpr int NB = swcorr_plan_s::kBands;
+  if (!p->hs_in) {
+    bool ok = cudaStreamCreateWithFlags(&p->hs_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->hs_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->he_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; ok && b < NB; b++)
+      ok = cudaStreamCreateWithFlags(&p->hs_k[b], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p->he_in[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p->he_k[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail(cudaGetLastError(), "host-run streams and events");
+  }
+  const Scene2D& sc = p->k2.sc;
+  const int64_t W = p->shape[1], H = p->shape[0];
+  const size_t eb = elem_size(p->dtype);
+  const int64_t OW = p->oshape[1];
+  // bind the staging buffers once (tensor maps of the whole staged image)
+  const bool cached = p->d_x == p->cached_x && p->d_y == p->cached_y && W == p->cached_pitch;
+  bool use_tma = false;
+  swcorr_status s1 = bind_2d(&p->k2, p->g2, p->dtype, p->d_x, p->d_y, W, p->d_c, OW, nullptr, !cached, &use_tma);
+  if (s1 != SWCORR_OK) {
+    p->cached_x = p->cached_y = nullptr;
+    return s1;
+  }
+  if (use_tma) {
+    p->cached_x = p->d_x;
+    p->cached_y = p->d_y;
+    p->cached_pitch = W;
+  }
+  // work already queued on the caller's stream comes first
+  if ((e = cudaEventRecord(p->he_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(p->hs_in, p->he_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "order host run after the caller's stream");
+  const int n_rb = sc.n_rb;
+  const int nb = std::min(NB, n_rb);
+  int64_t rows_in = 0;  // input rows copied so far
+  const unsigned char* hx = static_cast<const unsigned char*>(x);
+  const unsigned char* hy = static_cast<const unsigned char*>(y);
+  unsigned char* dx = static_cast<unsigned char*>(p->d_x);
+  unsigned char* dy = static_cast<unsigned char*>(p->d_y);
+  for (int b = 0; b < nb; b++) {
+    const int rb0 = (int)((int64_t)n_rb * b / nb), rb1 = (int)((int64_t)n_rb * (b + 1) / nb);
+    const int64_t j1 = std::min<int64_t>((int64_t)rb1 * sc.TJ, sc.OH);  // output rows [rb0 TJ, j1)
+    const int64_t need = std::min<int64_t>(H, (j1 - 1) * sc.sy + sc.h2 + 1);  // input rows the band reads
+    if (need > rows_in) {
+      const size_t off = (size_t)rows_in * W * eb, bytes = (size_t)(need - rows_in) * W * eb;
+      if ((e = cudaMemcpyAsync(dx + off, hx + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dy + off, hy + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess)
+        return cuda_fail(e, "copy input band to device");
+      rows_in = need;
+    }
+    if ((e = cudaEventRecord(p->he_in[b], p->hs_in)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->hs_k[b], p->he_in[b], 0)) != cudaSuccess)
+      return cuda_fail(e, "band input event");
+    K2DParams kp = p->k2;
+    kp.rb0 = rb0;
+    kp.n_items = (rb1 - rb0) * sc.n_strips;
+    const int grid = std::min(kp.n_items, p->grid);
+    e = p->dtype == SWCORR_F32 ? k2d_f32_launch(sc.kw, kp, grid, p->smem, p->hs_k[b], use_tma)
+                               : k2d_u16_launch(sc.kw, kp, grid, p->smem, p->hs_k[b], use_tma);
+    if (e != cudaSuccess) return cuda_fail(e, "2-D band kernel launch");
+    if ((e = cudaEventRecord(p->he_k[b], p->hs_k[b])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->hs_out, p->he_k[b], 0)) != cudaSuccess)
+      return cuda_fail(e, "band kernel event");
+    const int64_t o0 = (int64_t)rb0 * sc.TJ;
+    const size_t ooff = (size_t)o0 * OW * sizeof(float), obytes = (size_t)(j1 - o0) * OW * sizeof(float);
+    if ((e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(c) + ooff,
+                             reinterpret_cast<unsigned char*>(p->d_c) + ooff, obytes, cudaMemcpyDeviceToHost,
+                             p->hs_out)) != cudaSuccess)
+      return cuda_fail(e, "copy output band to host");
+  }
+  if ((e = cudaStreamSynchronize(p->hs_out)) != cudaSuccess) return cuda_fail(e, "host run synchronize");
+  return SWCORR_OK;
+}
+
 swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream) {
   g_last_error.clear();
   if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
@@ -701,6 +788,7 @@ swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float
   if (p->ndim >= 2 && (inner * (int64_t)elem_size(p->dtype)) % 16 != 0)
     return fail(SWCORR_ERR_ALIGNMENT, "host runs need rows of a multiple of 16 bytes (got %lld elements)",
                 (long long)inner);
+  if (p->kind == KIND_2D_U16 || p->kind == KIND_2D_F32) return run_host_2d_banded(p, x, y, c, st);
   if ((e = cudaMemcpyAsync(p->d_x, x, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "copy x to device");
   if ((e = cudaMemcpyAsync(p->d_y, y, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -745,6 +833,14 @@ void swcorr_plan_destroy(swcorr_plan p) {
   cudaFree(p->d_x);
   cudaFree(p->d_y);
   cudaFree(p->d_c);
+  if (p->hs_in) cudaStreamDestroy(p->hs_in);
+  if (p->hs_out) cudaStreamDestroy(p->hs_out);
+  if (p->he_start) cudaEventDestroy(p->he_start);
+  for (int b = 0; b < swcorr_plan_s::kBands; b++) {
+    if (p->hs_k[b]) cudaStreamDestroy(p->hs_k[b]);
+    if (p->he_in[b]) cudaEventDestroy(p->he_in[b]);
+    if (p->he_k[b]) cudaEventDestroy(p->he_k[b]);
+  }
   delete p;
 }
 
