@@ -464,10 +464,11 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   return true;
 }
 
-// One warp per CTA, persistent over the plan's work items (the 64-bit
-// engine is held to 12 resident CTAs per SM up to 17 columns, 8 above).
+// One warp per CTA, persistent over the plan's work items: 16 resident CTAs
+// per SM for the 32-bit engine; the 64-bit engine is held to 12 up to 17
+// columns, 8 above.
 template <int M, int KW, bool TMA, bool WIDE>
-__global__ void __launch_bounds__(32, WIDE ? (KW <= 17 ? 12 : 8) : 1) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
+__global__ void __launch_bounds__(32, WIDE ? (KW <= 17 ? 12 : 8) : 16) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
   using G = Geo2D<M, KW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring2D rg;
