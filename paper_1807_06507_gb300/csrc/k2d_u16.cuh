@@ -257,7 +257,10 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
   int until_out = sc.kh - 1;  // rows until the next output row is complete
   int jr = j0;
 
-  for (int i = 0; i < nrows; i++) {
+  // One row step; LEAVE is false for the first kh rows of the item, which
+  // have no leaving row (their row pass works on the entering row alone).
+  auto step = [&](int i, auto leave_tag) -> bool {
+    constexpr bool LEAVE = decltype(leave_tag)::value;
     __syncwarp();
     if (i + PF < nrows && (!TMA || lane == 0)) {
       if (TMA) fence_proxy_async_smem();
@@ -276,7 +279,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       }
       return false;
     }
-    const bool has_leave = i >= sc.kh;
+    constexpr bool has_leave = LEAVE;
 
     uint32_t we[G::NWORD], wl[G::NWORD], ye[G::NWORD], yl[G::NWORD];
     {
@@ -289,7 +292,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
         we[4 * h] = a.x; we[4 * h + 1] = a.y; we[4 * h + 2] = a.z; we[4 * h + 3] = a.w;
         ye[4 * h] = b.x; ye[4 * h + 1] = b.y; ye[4 * h + 2] = b.z; ye[4 * h + 3] = b.w;
       }
-      if (has_leave) {
+      if constexpr (has_leave) {
         const uint16_t* pl = rg.lx + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
         const uint16_t* ql = rg.ly + (size_t)s * G::RWS + M * lane + G::CH0 * 8;
 #pragma unroll
@@ -459,6 +462,14 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
       jr++;
     }
     until_out--;
+    return true;
+  };
+  {
+    const int nw = min(sc.kh, nrows);
+    for (int i = 0; i < nw; i++)
+      if (!step(i, std::false_type{})) return false;
+    for (int i = nw; i < nrows; i++)
+      if (!step(i, std::true_type{})) return false;
   }
   seq += (uint32_t)nrows;
   return true;
