@@ -29,6 +29,8 @@
 //    rounds once to float32 per factor.  A zero variance gives NaN exactly.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kparams.h"
 
@@ -172,7 +174,11 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         }
         return false;
       }
-      body(i, s);
+      // the first kh rows of an item have no leaving row (compile-time phase)
+      if (i < sc.kh)
+        body(i, s, std::false_type{});
+      else
+        body(i, s, std::true_type{});
       s = (s + 1 == NR) ? 0u : s + 1;
       if (s == 0u) lap ^= 1u;
     }
@@ -190,7 +196,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
-  if (!stream_rows(false, [&](int i, uint32_t s) {
+  if (!stream_rows(false, [&](int i, uint32_t s, auto) {
         if (t0 + i < 0 || t0 + i >= sc.H) return;
         const float* px = lane_ptr(rg.rx, s);
         const float* py = lane_ptr(rg.ry, s);
@@ -238,8 +244,8 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   const uint32_t seq0 = seq;
 
   // ---- pass 2: the D-march on fixed-point values
-  const bool ok = stream_rows(true, [&](int i, uint32_t s) {
-    const bool has_leave = i >= sc.kh;
+  const bool ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
+    constexpr bool has_leave = decltype(leave_tag)::value;
     const float* pxe = lane_ptr(rg.rx, s);
     const float* pye = lane_ptr(rg.ry, s);
     const float* pxl = lane_ptr(rg.lx, s);
@@ -260,7 +266,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
       const float4 a = *reinterpret_cast<const float4*>(pxe + 4 * h);
       const float4 b = *reinterpret_cast<const float4*>(pye + 4 * h);
       float4 al = make_float4(0.f, 0.f, 0.f, 0.f), bl = al;
-      if (has_leave) {
+      if constexpr (has_leave) {
         al = *reinterpret_cast<const float4*>(pxl + 4 * h);
         bl = *reinterpret_cast<const float4*>(pyl + 4 * h);
       }
@@ -270,8 +276,8 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
       for (int u = 0; u < 4; u++) {
         const int e = 4 * h + u - G::E0;
         if (e < 0 || e >= G::NCOL) continue;
-        const int Xe = quant(xa[u], qxe), Xl = quant(xla[u], qxl);
-        const int Ye = quant(ya[u], qye), Yl = quant(yla[u], qyl);
+        const int Xe = quant(xa[u], qxe), Xl = has_leave ? quant(xla[u], qxl) : 0;
+        const int Ye = quant(ya[u], qye), Yl = has_leave ? quant(yla[u], qyl) : 0;
         const int D = (int)((uint32_t)Xe - (uint32_t)Xl), S = (int)((uint32_t)Xe + (uint32_t)Xl);
         const int Dy = (int)((uint32_t)Ye - (uint32_t)Yl), Sy = (int)((uint32_t)Ye + (uint32_t)Yl);
         P0 += (uint32_t)D;
