@@ -88,6 +88,18 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// int64 -> float32 through two 32-bit halves, v = hi * 2^32 + lo with lo the
+// low word read as signed (so lo in [-2^31, 2^31) and hi = round-half-up of
+// v / 2^32). For |v| < 2^31, hi = 0 and the result is v correctly rounded;
+// above that |v| >= 2^31 and the three roundings (hi when |hi| > 2^24, lo,
+// the fma) keep the relative error below 2^-22. Two 32-bit conversions and
+// an fma issue faster than one 64-bit conversion.
+__device__ __forceinline__ float i64_to_f32(long long v) {
+  const int lo = (int)(unsigned)(unsigned long long)v;
+  const int hi = (int)(v >> 32) + (int)((unsigned)lo >> 31);
+  return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
 // Clamp to [-1, 1] that keeps NaN (PTX max/min with .NaN).
 __device__ __forceinline__ float clamp1_nan(float v) {
   float r;

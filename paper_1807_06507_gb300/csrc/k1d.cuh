@@ -95,7 +95,7 @@ __device__ __forceinline__ float pearson_exact(const Sums5& s, uint32_t n) {
   const long long vy = (long long)((uint64_t)n * s.yy - (uint64_t)(sy * sy));
   const long long num = (long long)((uint64_t)n * s.xy - (uint64_t)(sx * sy));
   // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
-  return clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+  return clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
 }
 
 // Fixed-point map of a float32 chunk: m = midpoint of [lo, hi], scale 2^e

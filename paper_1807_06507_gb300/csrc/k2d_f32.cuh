@@ -326,7 +326,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         const long long vy = (long long)(n * V3[c] - s1 * s1);
         const long long num = (long long)(n * V4[c] - s0 * s1);
         // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
-        res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+        res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
       }
       if (fast_cols && cl + M <= sc.W) {
 #pragma unroll

@@ -373,7 +373,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
         const long long vx = (long long)(n * (uint64_t)VQ[c][0] - s0 * s0);
         const long long vy = (long long)(n * (uint64_t)VQ[c][1] - s1 * s1);
         const long long num = (long long)(n * (uint64_t)VQ[c][2] - s0 * s1);
-        res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+        res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
         const int cc = cl + c;
         if (sc.sums && cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) {
           long long* s5 = sc.sums + 5ll * ((long long)jr * sc.OW + (sc.sx == 1 ? cc : cc / sc.sx));

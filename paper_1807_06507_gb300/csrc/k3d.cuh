@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
             const long long vx = (long long)(n * V2[a][c] - s0 * s0);
             const long long vy = (long long)(n * V3[a][c] - s1 * s1);
             const long long num = (long long)(n * V4[a][c] - s0 * s1);
-            res[c] = clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+            res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
           }
           if (p.vec_store && xc0 + 3 < p.W) {
             stg128(orow + xc0, res[0], res[1], res[2], res[3]);
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
               const long long vy = (long long)(n * V3[a][c] - s1 * s1);
               const long long num = (long long)(n * V4[a][c] - s0 * s1);
               orow[xc / p.sx] =
-                  clamp1_nan(__ll2float_rn(num) * rsqrtf(__ll2float_rn(vx) * __ll2float_rn(vy)));
+                  clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
             }
           }
         }
