@@ -185,7 +185,12 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
 /* Same computation from HOST buffers: copies x and y to plan-owned device
  * staging buffers, runs, copies c back and synchronises the stream.  Host
  * buffers are contiguous; pinned memory gives the fastest copies.  The plan
- * allocates its staging buffers on the first call (SWCORR_ERR_OOM on failure). */
+ * allocates its staging buffers on the first call (SWCORR_ERR_OOM on failure).
+ * 2-D plans pipeline the copies and kernels over bands of rows.  When x, y
+ * and c are all page-locked, that pipeline is recorded once as a CUDA graph
+ * for those three pointers and replayed by later calls with the same
+ * pointers (their contents are read at each call); other pointers record a
+ * new graph.  A plan is not to be run from two host threads at once. */
 swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream);
 
 /* One scene of a batched plan.  Scenes are 2-D uint16 with square or

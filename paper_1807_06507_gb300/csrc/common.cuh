@@ -100,11 +100,11 @@ __device__ __forceinline__ float i64_to_f32(long long v) {
   return fmaf((float)hi, 4294967296.0f, (float)lo);
 }
 
-// Clamp to [-1, 1] that keeps NaN (PTX max/min with .NaN).
+// Clamp to [-1, 1] that keeps NaN, in one instruction: min of |v| and 1
+// with the sign of v (sign(v) xor sign(1)); .NaN propagates a NaN input.
 __device__ __forceinline__ float clamp1_nan(float v) {
   float r;
-  asm("max.NaN.f32 %0, %1, -1.0;" : "=f"(r) : "f"(v));
-  asm("min.NaN.f32 %0, %0, 1.0;" : "+f"(r));
+  asm("min.NaN.xorsign.abs.f32 %0, %1, 0f3F800000;" : "=f"(r) : "f"(v));
   return r;
 }
 

@@ -122,11 +122,6 @@ __device__ __forceinline__ void ldg_row_u16(uint16_t* dst, const uint16_t* src, 
   }
 }
 
-// Float of a small signed integer (|v| < 2^22) on the FMA/ALU pipes.
-__device__ __forceinline__ float small_int_to_float(int v) {
-  return __int_as_float(0x4B400000 + v) - 12582912.0f;
-}
-
 // Step 4 for one output from its exact modular window sums (see the file
 // header).  Valid when Sxx, Syy < 2^32 (certified by the caller) and
 // T_x T_y < 2^62, i.e. |U| < 2^31: the caller checks tt = T_x T_y.
@@ -136,7 +131,7 @@ __device__ __forceinline__ float pearson_u16(uint32_t Sx, uint32_t Sy, uint32_t 
   const uint32_t Tx = Sxx - a * (Sx + (uint32_t)r);
   const uint32_t Ty = Syy - b * (Sy + (uint32_t)s);
   const int U = (int)(Sxy - b * Sx - a * (uint32_t)s);
-  const float fr = small_int_to_float(r), fs = small_int_to_float(s);
+  const float fr = __int2float_rn(r), fs = __int2float_rn(s);
   const float fTx = __uint2float_rn(Tx), fTy = __uint2float_rn(Ty);
   tt = fTx * fTy;
   const float vx = fmaf(fn, fTx, -fr * fr);
@@ -479,7 +474,7 @@ __device__ __forceinline__ bool process_item_2d_u16(const Scene2D& sc, int strip
 // per SM for the 32-bit engine; the 64-bit engine is held to 12 up to 17
 // columns, 8 above.
 template <int M, int KW, bool TMA, bool WIDE>
-__global__ void __launch_bounds__(32, WIDE ? (KW <= 17 ? 12 : 8) : 16) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
+__global__ void __launch_bounds__(32, WIDE ? (KW <= 17 ? 12 : 8) : (KW <= 3 ? 16 : 12)) k2d_u16_kernel(const __grid_constant__ K2DParams p) {
   using G = Geo2D<M, KW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring2D rg;

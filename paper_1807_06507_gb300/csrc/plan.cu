@@ -304,11 +304,20 @@ struct swcorr_plan_s {
   void* d_y = nullptr;
   float* d_c = nullptr;
   // banded host runs of 2-D plans: input copies, band kernels, output copies
+  // (kBands bands on the stream path, kGraphBands in the recorded graph)
   static constexpr int kBands = 8;
-  cudaStream_t hs_in = nullptr, hs_out = nullptr;
+  static constexpr int kGraphBands = 5;
+  static constexpr int kMaxBands = 16;
+  cudaStream_t hs_in = nullptr, hs_out = nullptr, hs_cap = nullptr;
   cudaStream_t hs_k[kBands] = {};
-  cudaEvent_t he_start = nullptr;
-  cudaEvent_t he_in[kBands] = {}, he_k[kBands] = {};
+  cudaEvent_t he_start = nullptr, he_done = nullptr;
+  cudaEvent_t he_in[kMaxBands] = {}, he_k[kMaxBands] = {};
+  // the recorded host-run graph and the host buffers it was recorded for
+  cudaGraphExec_t hgraph_exec = nullptr;
+  const void* hg_x = nullptr;
+  const void* hg_y = nullptr;
+  const void* hg_c = nullptr;
+  bool hg_tma = false;
 };
 
 static int64_t n_outputs(const swcorr_plan_s* p) {
@@ -681,24 +690,116 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
 // a band needs (its rows plus the window halo) are copied in order on one
 // stream; each band's kernel launch waits only for its own input and runs on
 // its own stream, so band kernels overlap each other and the copies; each
-// band's output rows go back as soon as its kernel ends.  Synchronous, like
-// swcorr_run_host.
+// band's output rows go back as soon as its kernel ends.  The work forks from
+// and joins back to `origin`.
+static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const void* x, const void* y, float* c,
+                                    bool use_tma, const int* weights, int nb_max, cudaStream_t origin) {
+  cudaError_t e;
+  const Scene2D& sc = k2.sc;
+  const int64_t W = p->shape[1], H = p->shape[0];
+  const size_t eb = elem_size(p->dtype);
+  const int64_t OW = p->oshape[1];
+  if ((e = cudaEventRecord(p->he_start, origin)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(p->hs_in, p->he_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "order host run after the caller's stream");
+  const int n_rb = sc.n_rb;
+  const int nb = std::min(nb_max, n_rb);
+  // band b covers row blocks [rbs[b], rbs[b + 1]): weights give the shares
+  // (small first and last bands shorten the pipeline's fill and drain)
+  int rbs[swcorr_plan_s::kMaxBands + 1];
+  {
+    int64_t tot = 0, acc = 0;
+    for (int b = 0; b < nb; b++) tot += nb == nb_max ? weights[b] : 1;
+    rbs[0] = 0;
+    for (int b = 0; b < nb; b++) {
+      acc += nb == nb_max ? weights[b] : 1;
+      rbs[b + 1] = (int)((int64_t)n_rb * acc / tot);
+    }
+  }
+  int64_t rows_in = 0;  // input rows copied so far
+  bool used[swcorr_plan_s::kBands] = {};
+  const unsigned char* hx = static_cast<const unsigned char*>(x);
+  const unsigned char* hy = static_cast<const unsigned char*>(y);
+  unsigned char* dx = static_cast<unsigned char*>(p->d_x);
+  unsigned char* dy = static_cast<unsigned char*>(p->d_y);
+  for (int b = 0; b < nb; b++) {
+    const int rb0 = rbs[b], rb1 = rbs[b + 1];
+    if (rb1 <= rb0) continue;
+    const int64_t j1 = std::min<int64_t>((int64_t)rb1 * sc.TJ, sc.OH);  // output rows [rb0 TJ, j1)
+    const int64_t need = std::min<int64_t>(H, (j1 - 1) * sc.sy + sc.h2 + 1);  // input rows the band reads
+    if (need > rows_in) {
+      const size_t off = (size_t)rows_in * W * eb, bytes = (size_t)(need - rows_in) * W * eb;
+      if ((e = cudaMemcpyAsync(dx + off, hx + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dy + off, hy + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess)
+        return cuda_fail(e, "copy input band to device");
+      rows_in = need;
+    }
+    cudaStream_t sk = p->hs_k[b % swcorr_plan_s::kBands];
+    used[b % swcorr_plan_s::kBands] = true;
+    if ((e = cudaEventRecord(p->he_in[b], p->hs_in)) != cudaSuccess || (e = cudaStreamWaitEvent(sk, p->he_in[b], 0)) != cudaSuccess)
+      return cuda_fail(e, "band input event");
+    K2DParams kp = k2;
+    kp.rb0 = rb0;
+    kp.n_items = (rb1 - rb0) * sc.n_strips;
+    const int grid = std::min(kp.n_items, p->grid);
+    e = p->dtype == SWCORR_F32 ? k2d_f32_launch(sc.kw, kp, grid, p->smem, sk, use_tma)
+                               : k2d_u16_launch(sc.kw, kp, grid, p->smem, sk, use_tma);
+    if (e != cudaSuccess) return cuda_fail(e, "2-D band kernel launch");
+    if ((e = cudaEventRecord(p->he_k[b], sk)) != cudaSuccess || (e = cudaStreamWaitEvent(p->hs_out, p->he_k[b], 0)) != cudaSuccess)
+      return cuda_fail(e, "band kernel event");
+    const int64_t o0 = (int64_t)rb0 * sc.TJ;
+    const size_t ooff = (size_t)o0 * OW * sizeof(float), obytes = (size_t)(j1 - o0) * OW * sizeof(float);
+    if ((e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(c) + ooff,
+                             reinterpret_cast<unsigned char*>(p->d_c) + ooff, obytes, cudaMemcpyDeviceToHost,
+                             p->hs_out)) != cudaSuccess)
+      return cuda_fail(e, "copy output band to host");
+  }
+  // join every forked stream back to the origin
+  if ((e = cudaEventRecord(p->he_done, p->hs_out)) != cudaSuccess || (e = cudaStreamWaitEvent(origin, p->he_done, 0)) != cudaSuccess ||
+      (e = cudaEventRecord(p->he_in[0], p->hs_in)) != cudaSuccess || (e = cudaStreamWaitEvent(origin, p->he_in[0], 0)) != cudaSuccess)
+    return cuda_fail(e, "join host run");
+  for (int b = 0; b < swcorr_plan_s::kBands; b++)
+    if (used[b] && ((e = cudaEventRecord(p->he_k[b], p->hs_k[b])) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(origin, p->he_k[b], 0)) != cudaSuccess))
+      return cuda_fail(e, "join host run");
+  return SWCORR_OK;
+}
+
+// Band shares of the recorded pipeline: small first and last bands shorten
+// the fill (input copy of the first band, alone) and the drain (output copy
+// of the last band, alone); the middle bands overlap both directions.
+static const int kGraphBandWeights[swcorr_plan_s::kGraphBands] = {1, 4, 6, 4, 1};
+static const int kStreamBandWeights[swcorr_plan_s::kBands] = {1, 1, 1, 1, 1, 1, 1, 1};
+
+static bool page_locked(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Synchronous, like swcorr_run_host.  With page-locked x, y and c the band
+// pipeline is recorded once as a CUDA graph (keyed by the three pointers)
+// and replayed with one launch, so the host issues one call instead of about
+// ten per band; pageable buffers take the stream path.
 static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const void* y, float* c, cudaStream_t st) {
   cudaError_t e;
-  constexpr int NB = swcorr_plan_s::kBands;
   if (!p->hs_in) {
     bool ok = cudaStreamCreateWithFlags(&p->hs_in, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&p->hs_out, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&p->he_start, cudaEventDisableTiming) == cudaSuccess;
-    for (int b = 0; ok && b < NB; b++)
-      ok = cudaStreamCreateWithFlags(&p->hs_k[b], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&p->he_in[b], cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->hs_cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->he_start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->he_done, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; ok && b < swcorr_plan_s::kBands; b++)
+      ok = cudaStreamCreateWithFlags(&p->hs_k[b], cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b < swcorr_plan_s::kMaxBands; b++)
+      ok = cudaEventCreateWithFlags(&p->he_in[b], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&p->he_k[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) return cuda_fail(cudaGetLastError(), "host-run streams and events");
   }
-  const Scene2D& sc = p->k2.sc;
-  const int64_t W = p->shape[1], H = p->shape[0];
-  const size_t eb = elem_size(p->dtype);
+  const int64_t W = p->shape[1];
   const int64_t OW = p->oshape[1];
   // bind the staging buffers once (tensor maps of the whole staged image)
   const bool cached = p->d_x == p->cached_x && p->d_y == p->cached_y && W == p->cached_pitch;
@@ -713,48 +814,39 @@ static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const v
     p->cached_y = p->d_y;
     p->cached_pitch = W;
   }
-  // work already queued on the caller's stream comes first
-  if ((e = cudaEventRecord(p->he_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(p->hs_in, p->he_start, 0)) != cudaSuccess)
-    return cuda_fail(e, "order host run after the caller's stream");
-  const int n_rb = sc.n_rb;
-  const int nb = std::min(NB, n_rb);
-  int64_t rows_in = 0;  // input rows copied so far
-  const unsigned char* hx = static_cast<const unsigned char*>(x);
-  const unsigned char* hy = static_cast<const unsigned char*>(y);
-  unsigned char* dx = static_cast<unsigned char*>(p->d_x);
-  unsigned char* dy = static_cast<unsigned char*>(p->d_y);
-  for (int b = 0; b < nb; b++) {
-    const int rb0 = (int)((int64_t)n_rb * b / nb), rb1 = (int)((int64_t)n_rb * (b + 1) / nb);
-    const int64_t j1 = std::min<int64_t>((int64_t)rb1 * sc.TJ, sc.OH);  // output rows [rb0 TJ, j1)
-    const int64_t need = std::min<int64_t>(H, (j1 - 1) * sc.sy + sc.h2 + 1);  // input rows the band reads
-    if (need > rows_in) {
-      const size_t off = (size_t)rows_in * W * eb, bytes = (size_t)(need - rows_in) * W * eb;
-      if ((e = cudaMemcpyAsync(dx + off, hx + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess ||
-          (e = cudaMemcpyAsync(dy + off, hy + off, bytes, cudaMemcpyHostToDevice, p->hs_in)) != cudaSuccess)
-        return cuda_fail(e, "copy input band to device");
-      rows_in = need;
+  bool graphed = false;
+  if (page_locked(x) && page_locked(y) && page_locked(c)) {
+    if (!p->hgraph_exec || p->hg_x != x || p->hg_y != y || p->hg_c != c || p->hg_tma != use_tma) {
+      if (p->hgraph_exec) cudaGraphExecDestroy(p->hgraph_exec);
+      p->hgraph_exec = nullptr;
+      // record; if anything in the recording fails, the stream path below
+      // runs instead (and reports a real error itself)
+      if (cudaStreamBeginCapture(p->hs_cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        swcorr_status s2 =
+            enqueue_banded(p, p->k2, x, y, c, use_tma, kGraphBandWeights, swcorr_plan_s::kGraphBands, p->hs_cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->hs_cap, &g);
+        if (s2 == SWCORR_OK && e == cudaSuccess && g && cudaGraphInstantiate(&p->hgraph_exec, g, 0) != cudaSuccess)
+          p->hgraph_exec = nullptr;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+      g_last_error.clear();
+      p->hg_x = x;
+      p->hg_y = y;
+      p->hg_c = c;
+      p->hg_tma = use_tma;
     }
-    if ((e = cudaEventRecord(p->he_in[b], p->hs_in)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(p->hs_k[b], p->he_in[b], 0)) != cudaSuccess)
-      return cuda_fail(e, "band input event");
-    K2DParams kp = p->k2;
-    kp.rb0 = rb0;
-    kp.n_items = (rb1 - rb0) * sc.n_strips;
-    const int grid = std::min(kp.n_items, p->grid);
-    e = p->dtype == SWCORR_F32 ? k2d_f32_launch(sc.kw, kp, grid, p->smem, p->hs_k[b], use_tma)
-                               : k2d_u16_launch(sc.kw, kp, grid, p->smem, p->hs_k[b], use_tma);
-    if (e != cudaSuccess) return cuda_fail(e, "2-D band kernel launch");
-    if ((e = cudaEventRecord(p->he_k[b], p->hs_k[b])) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(p->hs_out, p->he_k[b], 0)) != cudaSuccess)
-      return cuda_fail(e, "band kernel event");
-    const int64_t o0 = (int64_t)rb0 * sc.TJ;
-    const size_t ooff = (size_t)o0 * OW * sizeof(float), obytes = (size_t)(j1 - o0) * OW * sizeof(float);
-    if ((e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(c) + ooff,
-                             reinterpret_cast<unsigned char*>(p->d_c) + ooff, obytes, cudaMemcpyDeviceToHost,
-                             p->hs_out)) != cudaSuccess)
-      return cuda_fail(e, "copy output band to host");
+    if (p->hgraph_exec) {
+      if ((e = cudaGraphLaunch(p->hgraph_exec, st)) != cudaSuccess) return cuda_fail(e, "launch host-run graph");
+      graphed = true;
+    }
   }
-  if ((e = cudaStreamSynchronize(p->hs_out)) != cudaSuccess) return cuda_fail(e, "host run synchronize");
+  if (!graphed) {
+    swcorr_status s2 = enqueue_banded(p, p->k2, x, y, c, use_tma, kStreamBandWeights, swcorr_plan_s::kBands, st);
+    if (s2 != SWCORR_OK) return s2;
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "host run synchronize");
   return SWCORR_OK;
 }
 
@@ -833,11 +925,15 @@ void swcorr_plan_destroy(swcorr_plan p) {
   cudaFree(p->d_x);
   cudaFree(p->d_y);
   cudaFree(p->d_c);
+  if (p->hgraph_exec) cudaGraphExecDestroy(p->hgraph_exec);
   if (p->hs_in) cudaStreamDestroy(p->hs_in);
   if (p->hs_out) cudaStreamDestroy(p->hs_out);
+  if (p->hs_cap) cudaStreamDestroy(p->hs_cap);
   if (p->he_start) cudaEventDestroy(p->he_start);
-  for (int b = 0; b < swcorr_plan_s::kBands; b++) {
+  if (p->he_done) cudaEventDestroy(p->he_done);
+  for (int b = 0; b < swcorr_plan_s::kBands; b++)
     if (p->hs_k[b]) cudaStreamDestroy(p->hs_k[b]);
+  for (int b = 0; b < swcorr_plan_s::kMaxBands; b++) {
     if (p->he_in[b]) cudaEventDestroy(p->he_in[b]);
     if (p->he_k[b]) cudaEventDestroy(p->he_k[b]);
   }

@@ -99,3 +99,16 @@ def test_host_run(sw):
     p = sw.Plan(x.shape, 7, dtype="f32")
     ch = p.run_host(x, y)
     check(ch, x, y, 7)
+
+
+def test_host_run_pinned(sw):
+    import torch
+    x, y = W.uniform_pair((300, 512), seed=10)
+    p = sw.Plan(x.shape, 9, dtype="f32")
+    hx = torch.from_numpy(x).pin_memory().numpy()
+    hy = torch.from_numpy(y).pin_memory().numpy()
+    c = torch.empty(p.oshape, dtype=torch.float32).pin_memory().numpy()
+    for _ in range(2):  # record, then replay
+        c[...] = 0.0
+        p.run_host(hx, hy, c)
+        check(c, x, y, 9)

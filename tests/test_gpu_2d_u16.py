@@ -206,6 +206,45 @@ def test_night_scene_full_size(sw):
     assert n_sc > 11_000_000
 
 
+def _pinned(a, torch):
+    t = torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).pin_memory()
+    v = t.numpy()
+    return (v.view(np.uint16) if a.dtype == np.uint16 else v), t
+
+
+@pytest.mark.parametrize("stride", [None, (2, 3)])
+def test_host_run_pinned_graph(sw, stride):
+    # page-locked buffers take the recorded-graph path: a replay must read the
+    # buffers' current contents, and new buffers must re-record
+    import torch
+    shape = (530, 1000)
+    x0, y0 = W.night_scene(shape, seed=21)
+    x1, y1 = W.night_scene(shape, seed=22)
+    p = sw.Plan(shape, 7, stride, dtype="u16")
+    hx, tx = _pinned(x0, torch)
+    hy, ty = _pinned(y0, torch)
+    c = torch.empty(p.oshape, dtype=torch.float32).pin_memory().numpy()
+
+    def dev(x, y):
+        r = p.run(to_dev(x, torch), to_dev(y, torch))
+        torch.cuda.synchronize()
+        return r.cpu().numpy()
+
+    p.run_host(hx, hy, c)
+    assert np.array_equal(c, dev(x0, y0), equal_nan=True)
+    hx[...] = x1
+    hy[...] = y1
+    c[...] = 7.0
+    p.run_host(hx, hy, c)  # replay
+    assert np.array_equal(c, dev(x1, y1), equal_nan=True)
+    hx2, tx2 = _pinned(x0, torch)
+    c2 = torch.empty(p.oshape, dtype=torch.float32).pin_memory().numpy()
+    p.run_host(hx2, hy, c2)  # new buffers: re-recorded
+    assert np.array_equal(c2, dev(x0, y1), equal_nan=True)
+    score(c2, oracle.corr(x0, y1, 7, stride=stride))
+    p.check_status()
+
+
 def test_host_run_matches_device_run(sw):
     x, y = W.night_scene((200, 640), seed=13)
     p = sw.Plan(x.shape, 7, dtype="u16")
