@@ -26,6 +26,8 @@
 // All sums are modular integers (uint32 / uint64), hence exact.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kparams.h"
 
@@ -66,7 +68,9 @@ struct Geo3D {
   static constexpr int BXW = ((XH + TX + W2) + 7) / 8 * 8;  // box width (elements)
   static constexpr int COFF = XH - W1;             // column 0 of the footprint in the box
   static constexpr int VSP = TXI + 4;              // padded row of the vertical-sum buffer
+  static constexpr int LANES = TX / 4;             // lanes with output columns (4 each)
   static_assert(BXW <= 256, "box too wide");
+  static_assert(TX % 8 == 0 && TX <= 128, "footprint width must be a multiple of 8 of at most 128");
 };
 
 template <int TY, int TX, int KY, int KX>
@@ -83,6 +87,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
   unsigned char* slots = smem_raw;
   uint32_t* VS = reinterpret_cast<uint32_t*>(smem_raw + 2 * slot_bytes);  // [8][TY][VSP]
   uint64_t* bar = reinterpret_cast<uint64_t*>(VS + 8 * TY * G::VSP);      // 2 mbarriers (4 reserved)
+  static_assert(G::TXI <= K3_THREADS, "one input column per thread");
   __shared__ float red[4][K3_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -160,14 +165,16 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
         }
         if (!wait_slot(s & 1)) return;
         const int z = ze0 + s;
-        if (z >= 0 && z < p.Z) {
-          const float* px = reinterpret_cast<const float*>(slots + (s & 1) * slot_bytes);
+        // thread tid scans input column tid of the footprint down its rows
+        const int gxx = x0 - G::W1 + tid;
+        if (z >= 0 && z < p.Z && tid < G::TXI && gxx >= 0 && gxx < p.W) {
+          const float* px = reinterpret_cast<const float*>(slots + (s & 1) * slot_bytes) + G::COFF + tid;
           const float* py = px + yoff;
-          for (int e = tid; e < G::TYI * G::TXI; e += K3_THREADS) {
-            const int r = e / G::TXI, c = e - r * G::TXI;
-            const int gy = by + r, gxx = x0 - G::W1 + c;
-            if (gy >= 0 && gy < p.H && gxx >= 0 && gxx < p.W) {
-              const float a = px[r * G::BXW + G::COFF + c], b = py[r * G::BXW + G::COFF + c];
+#pragma unroll
+          for (int r = 0; r < G::TYI; r++) {
+            const int gy = by + r;
+            if (gy >= 0 && gy < p.H) {
+              const float a = px[r * G::BXW], b = py[r * G::BXW];
               xlo = fminf(xlo, a); xhi = fmaxf(xhi, a); ylo = fminf(ylo, b); yhi = fmaxf(yhi, b);
             }
           }
@@ -239,8 +246,10 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
       const unsigned char* se = slots;
       const unsigned char* sl = slots + slot_bytes;
 
-      // vertical pass: thread per input column
-      for (int c = tid; c < G::TXI; c += K3_THREADS) {
+      // vertical pass: thread per input column; a footprint whose input rows
+      // all lie in the volume takes a variant without the per-row test
+      auto vcol = [&](int c, auto y_in_tag) {
+        constexpr bool Y_IN = decltype(y_in_tag)::value;
         const int gxx = x0 - G::W1 + c;
         const bool col_ok = gxx >= 0 && gxx < p.W;
         const float fse_x = (col_ok && ze_ok) ? qsx : 0.f, fsl_x = (col_ok && zl_ok) ? qsx : 0.f;
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
 #pragma unroll
         for (int r = 0; r < G::TYI; r++) {
           const int gy = by + r;
-          const bool row_ok = gy >= 0 && gy < p.H;
+          const bool row_ok = Y_IN || (gy >= 0 && gy < p.H);
           const int idx = r * G::BXW + G::COFF + c;
           int Xe, Xl, Ye, Yl;
           if (p.is_f32) {
@@ -301,6 +310,13 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
           }
         }
         (void)fsl_y;
+      };
+      const bool y_in = by >= 0 && by + G::TYI <= p.H;
+      for (int c = tid; c < G::TXI; c += K3_THREADS) {
+        if (y_in)
+          vcol(c, std::true_type{});
+        else
+          vcol(c, std::false_type{});
       }
       __syncthreads();
       // both slots are free: request step s + 1
@@ -311,8 +327,11 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
       }
 
       // horizontal pass: warp -> 2 output rows, lane -> 4 output columns
+      // (lanes past the footprint's TX columns have none)
+      const bool lane_on = lane < G::LANES;
 #pragma unroll
       for (int a = 0; a < 2; a++) {
+        if (!lane_on) break;
         const int y = warp * 2 + a;
         uint32_t Q0 = 0u, Q1 = 0u;
         uint64_t Q2 = 0ull, Q3 = 0ull, Q4 = 0ull;
@@ -342,7 +361,8 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
       }
 
       // step 4 for the output plane whose window is complete
-      if (s >= p.kz - 1 && p.unit_stride) {
+      if (!lane_on) {
+      } else if (s >= p.kz - 1 && p.unit_stride) {
         // unit strides: output (z, y, x) = centre (z, y, x); 4 columns per lane
         const int zc = zc0 + (s - (p.kz - 1));
         const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;
