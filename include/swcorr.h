@@ -190,7 +190,10 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
  * and c are all page-locked, that pipeline is recorded once as a CUDA graph
  * for those three pointers and replayed by later calls with the same
  * pointers (their contents are read at each call); other pointers record a
- * new graph.  A plan is not to be run from two host threads at once. */
+ * new graph.  In that case the kernels store c directly through its device
+ * mapping (zero-copy) instead of a staging buffer and a copy back; c must
+ * then not be read or written by the host until the call returns.  A plan is
+ * not to be run from two host threads at once. */
 swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream);
 
 /* One scene of a batched plan.  Scenes are 2-D uint16 with square or

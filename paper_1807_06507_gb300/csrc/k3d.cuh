@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
           for (int c = 0; c < 4; c++) {
             const int xc = xc0 + c;
             const int cx = max(min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1, 0);
-            const uint64_t n = (uint64_t)(uint32_t)(cz * cy) * (uint64_t)cx;
+            // n <= 32768 * 15: a 32-bit count keeps n * sum a 32 x 64-bit product
+            const uint64_t n = (uint32_t)(cz * cy * cx);
             const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
             const long long vx = (long long)(n * V2[a][c] - s0 * s0);
             const long long vy = (long long)(n * V3[a][c] - s1 * s1);
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
               const int xc = x0 + 4 * lane + c;
               if (xc >= p.W || xc % p.sx != 0) continue;
               const int cx = min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1;
-              const uint64_t n = (uint64_t)cz * (uint64_t)cy * (uint64_t)cx;
+              const uint64_t n = (uint32_t)(cz * cy * cx);
               const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
               const long long vx = (long long)(n * V2[a][c] - s0 * s0);
               const long long vy = (long long)(n * V3[a][c] - s1 * s1);

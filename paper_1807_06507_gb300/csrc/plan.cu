@@ -693,7 +693,7 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
 // band's output rows go back as soon as its kernel ends.  The work forks from
 // and joins back to `origin`.
 static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const void* x, const void* y, float* c,
-                                    bool use_tma, const int* weights, int nb_max, cudaStream_t origin) {
+                                    float* c_dev, bool use_tma, const int* weights, int nb_max, cudaStream_t origin) {
   cudaError_t e;
   const Scene2D& sc = k2.sc;
   const int64_t W = p->shape[1], H = p->shape[0];
@@ -740,6 +740,11 @@ static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const
       return cuda_fail(e, "band input event");
     K2DParams kp = k2;
     kp.rb0 = rb0;
+    if (c_dev) {  // the band kernel stores straight into the caller's page-locked c
+      kp.sc.out = c_dev;
+      kp.sc.out_pitch = OW;
+      kp.sc.vec_store = (sc.sx == 1 && (reinterpret_cast<uintptr_t>(c_dev) & 15) == 0 && (OW % 4) == 0) ? 1 : 0;
+    }
     kp.n_items = (rb1 - rb0) * sc.n_strips;
     const int grid = std::min(kp.n_items, p->grid);
     e = p->dtype == SWCORR_F32 ? k2d_f32_launch(sc.kw, kp, grid, p->smem, sk, use_tma)
@@ -747,6 +752,7 @@ static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const
     if (e != cudaSuccess) return cuda_fail(e, "2-D band kernel launch");
     if ((e = cudaEventRecord(p->he_k[b], sk)) != cudaSuccess || (e = cudaStreamWaitEvent(p->hs_out, p->he_k[b], 0)) != cudaSuccess)
       return cuda_fail(e, "band kernel event");
+    if (c_dev) continue;
     const int64_t o0 = (int64_t)rb0 * sc.TJ;
     const size_t ooff = (size_t)o0 * OW * sizeof(float), obytes = (size_t)(j1 - o0) * OW * sizeof(float);
     if ((e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(c) + ooff,
@@ -771,14 +777,20 @@ static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const
 static const int kGraphBandWeights[swcorr_plan_s::kGraphBands] = {1, 4, 6, 4, 1};
 static const int kStreamBandWeights[swcorr_plan_s::kBands] = {1, 1, 1, 1, 1, 1, 1, 1};
 
-static bool page_locked(const void* ptr) {
+static bool page_locked(const void* ptr, void** dev_alias = nullptr) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  if (dev_alias) *dev_alias = a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
   return a.type == cudaMemoryTypeHost;
 }
+
+// Band kernels of the recorded host run write c through its device mapping
+// (no separate output copies); the results then stream back over the host
+// link while later bands compute and their inputs arrive.
+static constexpr bool kDirectHostOutput = true;
 
 // Synchronous, like swcorr_run_host.  With page-locked x, y and c the band
 // pipeline is recorded once as a CUDA graph (keyed by the three pointers)
@@ -815,7 +827,9 @@ static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const v
     p->cached_pitch = W;
   }
   bool graphed = false;
-  if (page_locked(x) && page_locked(y) && page_locked(c)) {
+  void* c_alias = nullptr;
+  if (page_locked(x) && page_locked(y) && page_locked(c, &c_alias)) {
+    float* c_dev = kDirectHostOutput ? static_cast<float*>(c_alias) : nullptr;
     if (!p->hgraph_exec || p->hg_x != x || p->hg_y != y || p->hg_c != c || p->hg_tma != use_tma) {
       if (p->hgraph_exec) cudaGraphExecDestroy(p->hgraph_exec);
       p->hgraph_exec = nullptr;
@@ -823,7 +837,7 @@ static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const v
       // runs instead (and reports a real error itself)
       if (cudaStreamBeginCapture(p->hs_cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         swcorr_status s2 =
-            enqueue_banded(p, p->k2, x, y, c, use_tma, kGraphBandWeights, swcorr_plan_s::kGraphBands, p->hs_cap);
+            enqueue_banded(p, p->k2, x, y, c, c_dev, use_tma, kGraphBandWeights, swcorr_plan_s::kGraphBands, p->hs_cap);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(p->hs_cap, &g);
         if (s2 == SWCORR_OK && e == cudaSuccess && g && cudaGraphInstantiate(&p->hgraph_exec, g, 0) != cudaSuccess)
@@ -843,7 +857,7 @@ static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const v
     }
   }
   if (!graphed) {
-    swcorr_status s2 = enqueue_banded(p, p->k2, x, y, c, use_tma, kStreamBandWeights, swcorr_plan_s::kBands, st);
+    swcorr_status s2 = enqueue_banded(p, p->k2, x, y, c, nullptr, use_tma, kStreamBandWeights, swcorr_plan_s::kBands, st);
     if (s2 != SWCORR_OK) return s2;
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "host run synchronize");
