@@ -196,35 +196,26 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
-  // lanes whose columns all lie in the grid scan without the column test
-  const bool cols_in = e_lo == 0 && e_hi == G::NCOL;
-  auto scan_row = [&](uint32_t s, auto cols_in_tag) {
-    constexpr bool ALL_IN = decltype(cols_in_tag)::value;
-    const float* px = lane_ptr(rg.rx, s);
-    const float* py = lane_ptr(rg.ry, s);
-#pragma unroll
-    for (int h = 0; h < G::NCH; h++) {
-      const float4 a = *reinterpret_cast<const float4*>(px + 4 * h);
-      const float4 b = *reinterpret_cast<const float4*>(py + 4 * h);
-      const float va[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int e = 4 * h + u - G::E0;
-        if (e >= 0 && e < G::NCOL && (ALL_IN || (e >= e_lo && e < e_hi))) {
-          xlo = fminf(xlo, va[u]);
-          xhi = fmaxf(xhi, va[u]);
-          ylo = fminf(ylo, vb[u]);
-          yhi = fmaxf(yhi, vb[u]);
-        }
-      }
-    }
-  };
   if (!stream_rows(false, [&](int i, uint32_t s, auto) {
         if (t0 + i < 0 || t0 + i >= sc.H) return;
-        if (cols_in)
-          scan_row(s, std::true_type{});
-        else
-          scan_row(s, std::false_type{});
+        const float* px = lane_ptr(rg.rx, s);
+        const float* py = lane_ptr(rg.ry, s);
+#pragma unroll
+        for (int h = 0; h < G::NCH; h++) {
+          const float4 a = *reinterpret_cast<const float4*>(px + 4 * h);
+          const float4 b = *reinterpret_cast<const float4*>(py + 4 * h);
+          const float va[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int e = 4 * h + u - G::E0;
+            if (e >= 0 && e < G::NCOL && e >= e_lo && e < e_hi) {
+              xlo = fminf(xlo, va[u]);
+              xhi = fmaxf(xhi, va[u]);
+              ylo = fminf(ylo, vb[u]);
+              yhi = fmaxf(yhi, vb[u]);
+            }
+          }
+        }
       }))
     return false;
 
