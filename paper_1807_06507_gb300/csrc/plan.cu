@@ -772,8 +772,9 @@ static swcorr_status enqueue_banded(swcorr_plan_s* p, const K2DParams& k2, const
 }
 
 // Band shares of the recorded pipeline: small first and last bands shorten
-// the fill (input copy of the first band, alone) and the drain (output copy
-// of the last band, alone); the middle bands overlap both directions.
+// the fill (input copy of the first band, alone) and the tail (the last
+// band's kernel and its output, alone); the middle bands overlap both
+// directions of the host link.
 static const int kGraphBandWeights[swcorr_plan_s::kGraphBands] = {1, 4, 6, 4, 1};
 static const int kStreamBandWeights[swcorr_plan_s::kBands] = {1, 1, 1, 1, 1, 1, 1, 1};
 
@@ -858,7 +859,16 @@ static swcorr_status run_host_2d_banded(swcorr_plan_s* p, const void* x, const v
   }
   if (!graphed) {
     swcorr_status s2 = enqueue_banded(p, p->k2, x, y, c, nullptr, use_tma, kStreamBandWeights, swcorr_plan_s::kBands, st);
-    if (s2 != SWCORR_OK) return s2;
+    if (s2 != SWCORR_OK) {
+      // nothing queued so far may still touch the caller's buffers on return
+      const std::string msg = g_last_error;
+      cudaStreamSynchronize(p->hs_in);
+      for (int b = 0; b < swcorr_plan_s::kBands; b++) cudaStreamSynchronize(p->hs_k[b]);
+      cudaStreamSynchronize(p->hs_out);
+      cudaGetLastError();
+      g_last_error = msg;
+      return s2;
+    }
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "host run synchronize");
   return SWCORR_OK;

@@ -245,6 +245,27 @@ def test_host_run_pinned_graph(sw, stride):
     p.check_status()
 
 
+def test_host_run_mixed_page_locking(sw):
+    # only all-page-locked buffers take the recorded graph; every mix takes
+    # the stream path, and all give the device run's result
+    import torch
+    shape = (300, 512)
+    x, y = W.night_scene(shape, seed=23)
+    p = sw.Plan(shape, 5, dtype="u16")
+    ref = p.run(to_dev(x, torch), to_dev(y, torch))
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    hx, tx = _pinned(x, torch)
+    hy, ty = _pinned(y, torch)
+    pinned_c = torch.empty(p.oshape, dtype=torch.float32).pin_memory().numpy()
+    for xx, yy, cc in ((hx, hy, np.empty(p.oshape, np.float32)), (x.copy(), y.copy(), pinned_c),
+                       (hx, y.copy(), pinned_c), (hx, hy, pinned_c)):
+        cc[...] = 5.0
+        p.run_host(xx, yy, cc)
+        assert np.array_equal(cc, ref, equal_nan=True)
+    p.check_status()
+
+
 def test_host_run_matches_device_run(sw):
     x, y = W.night_scene((200, 640), seed=13)
     p = sw.Plan(x.shape, 7, dtype="u16")
