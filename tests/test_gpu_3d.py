@@ -65,3 +65,21 @@ def test_full_volume_stride2_and_sampled_stride1(sw):
     idx = rng.integers(0, c1.size, 1 << 18)
     ref, rx, ry = oracle.corr(x, y, 9, 1, idx=idx, relvar=True)
     score(c1.ravel()[idx], ref, rx, ry, exact_nan=False)
+
+
+def test_f32_padded_rows_ragged_edge(sw):
+    # rows of 150 floats in a 152-float pitch (TMA path, ragged last 16-byte
+    # group): the padding holds 1e30, which must stay out of every range
+    rng = np.random.default_rng(5)
+    shape = (18, 27, 150)
+    x = (3e3 + rng.standard_normal(shape)).astype(np.float32)
+    y = (0.3 * x + rng.standard_normal(shape)).astype(np.float32)
+    xp = np.full(shape[:2] + (152,), 1e30, np.float32)
+    yp = np.full(shape[:2] + (152,), -1e30, np.float32)
+    xp[..., :150], yp[..., :150] = x, y
+    p = sw.Plan(shape, (5, 9, 9), dtype="f32")
+    c = p.run(torch.from_numpy(xp).cuda()[..., :150], torch.from_numpy(yp).cuda()[..., :150])
+    torch.cuda.synchronize()
+    p.check_status()
+    ref, rx, ry = oracle.corr(x, y, (5, 9, 9), relvar=True)
+    score(c.cpu().numpy(), ref, rx, ry, exact_nan=False)
