@@ -93,3 +93,14 @@ def test_f32_strides_and_chunk_seams(sw, n, k, stride):
     c = run1(sw, x, y, k, stride)
     ref, rx, ry = oracle.corr(x, y, k, stride, relvar=True)
     score(c, ref, rx, ry, exact_nan=False)
+
+
+def test_host_run_1d(sw):
+    x, y = W.random_walk_pair(30_001, seed=41, flip=5000)
+    p = sw.Plan(x.shape, 301, 2, dtype="f32")
+    ref = p.run(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    torch.cuda.synchronize()
+    ch = p.run_host(x, y)
+    assert np.array_equal(ch, ref.cpu().numpy(), equal_nan=True)
+    p.check_status()
+

@@ -266,6 +266,25 @@ def test_host_run_mixed_page_locking(sw):
     p.check_status()
 
 
+@pytest.mark.parametrize("shape,k,stride", [((230, 640), 31, None), ((180, 512), (31, 3), None),
+                                             ((200, 520), (3, 31), (2, 1)), ((150, 600), 9, (1, 3))])
+def test_host_run_tall_windows_and_wide_engine(sw, shape, k, stride):
+    # band halos reach into earlier bands' rows; k >= 9 runs the 64-bit engine
+    import torch
+    x, y = W.night_scene(shape, seed=31)
+    p = sw.Plan(shape, k, stride, dtype="u16")
+    ref = p.run(to_dev(x, torch), to_dev(y, torch))
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    hx, tx = _pinned(x, torch)
+    hy, ty = _pinned(y, torch)
+    c = torch.empty(p.oshape, dtype=torch.float32).pin_memory().numpy()
+    p.run_host(hx, hy, c)  # recorded graph, direct output
+    assert np.array_equal(c, ref, equal_nan=True)
+    assert np.array_equal(p.run_host(x, y), ref, equal_nan=True)  # stream path
+    p.check_status()
+
+
 def test_host_run_matches_device_run(sw):
     x, y = W.night_scene((200, 640), seed=13)
     p = sw.Plan(x.shape, 7, dtype="u16")

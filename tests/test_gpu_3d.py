@@ -83,3 +83,22 @@ def test_f32_padded_rows_ragged_edge(sw):
     p.check_status()
     ref, rx, ry = oracle.corr(x, y, (5, 9, 9), relvar=True)
     score(c.cpu().numpy(), ref, rx, ry, exact_nan=False)
+
+
+@pytest.mark.parametrize("dtype", ["u16", "f32"])
+def test_host_run_3d(sw, dtype):
+    rng = np.random.default_rng(8)
+    shape = (12, 30, 136)
+    if dtype == "u16":
+        x = rng.integers(0, 4096, shape).astype(np.uint16)
+        y = rng.integers(0, 4096, shape).astype(np.uint16)
+    else:
+        x = (50 + rng.standard_normal(shape)).astype(np.float32)
+        y = (0.5 * x + rng.standard_normal(shape)).astype(np.float32)
+    p = sw.Plan(shape, (3, 5, 5), dtype=dtype)
+    ref = p.run(to_dev(x, torch), to_dev(y, torch))
+    torch.cuda.synchronize()
+    ch = p.run_host(x, y)
+    assert np.array_equal(ch, ref.cpu().numpy(), equal_nan=True)
+    p.check_status()
+
