@@ -44,24 +44,41 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    """Declare the C entry points' signatures on a loaded oracle library."""
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.swo_corr.argtypes = [ctypes.c_int, i64p, i32p, i32p, ctypes.c_int,
+                             ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
+                             dp, dp, dp, ctypes.c_int]
+    lib.swo_corr.restype = ctypes.c_int
+    lib.swo_sums_u16.argtypes = [ctypes.c_int, i64p, i32p, i32p,
+                                 ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
+                                 i64p, ctypes.c_int]
+    lib.swo_sums_u16.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            i32p = ctypes.POINTER(ctypes.c_int32)
-            dp = ctypes.POINTER(ctypes.c_double)
-            lib.swo_corr.argtypes = [ctypes.c_int, i64p, i32p, i32p, ctypes.c_int,
-                                     ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
-                                     dp, dp, dp, ctypes.c_int]
-            lib.swo_corr.restype = ctypes.c_int
-            lib.swo_sums_u16.argtypes = [ctypes.c_int, i64p, i32p, i32p,
-                                         ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
-                                         i64p, ctypes.c_int]
-            lib.swo_sums_u16.restype = ctypes.c_int
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _swap_library(path_or_lib):
+    """Tests only (planted-mistake checks): make later calls use another
+    build of the oracle -- a path to a shared library, a handle returned
+    earlier, or None for the regular build.  Returns the previous handle."""
+    global _lib
+    lib = path_or_lib
+    if isinstance(path_or_lib, (str, os.PathLike)):
+        lib = _configure(ctypes.CDLL(os.fspath(path_or_lib)))
+    with _lock:
+        prev, _lib = _lib, lib
+    return prev
 
 
 def _ptr(a, ct):

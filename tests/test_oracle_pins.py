@@ -218,6 +218,18 @@ def test_constant_window_with_offsets_is_nan():
         assert np.isnan(c[5, 5]) and np.isfinite(c[0, 0])
 
 
+def test_relvar_closed_form():
+    # relvar = sum (v - mean)^2 / sum v^2 over the window (whole grid here):
+    # x = 1, 2, 3: 2 / 14; y = 0, 0, 3: 6 / 9
+    x = np.array([1, 2, 3], dtype=np.uint16)
+    y = np.array([0, 0, 3], dtype=np.uint16)
+    c, rx, ry = oracle.corr(x, y, 3, relvar=True)
+    assert rx[1] == pytest.approx(1.0 / 7.0, rel=1e-15)
+    assert ry[1] == pytest.approx(2.0 / 3.0, rel=1e-15)
+    # Pearson of (1, 2, 3) and (0, 0, 3): sxy = 3, sxx = 2, syy = 6
+    assert c[1] == pytest.approx(3.0 / np.sqrt(12.0), rel=1e-15)
+
+
 # ------------------------------------------------------- exact integer sums
 def _sat_sums(x, y, k, stride):
     """Window sums via an int64 summed-area table (independent of the oracle)."""
