@@ -241,23 +241,37 @@ int64_t swcorr_plan_fallbacks(swcorr_plan p);
  * is a deployment variant of swcorr_run for a 2-D uint16 plan with stride 1,
  * computing the same results with the same kernel, but without a plan.
  *   rows, cols : grid size; kh, kw: window (kw odd, 1..31).
- *   x, y       : device uint16 grids; in_pitch elements between rows (<= 0
- *                means cols).  c: device float32 output, out_pitch elements
- *                between rows (<= 0 means cols).  stream: cudaStream_t.
+ *   x, y       : device uint16 grids (2-byte aligned); in_pitch elements
+ *                between rows (<= 0 means cols).  c: device float32 output
+ *                (4-byte aligned), out_pitch elements between rows (<= 0
+ *                means cols).  stream: cudaStream_t.
  * The kernel's scratch (its status words) lives in a 256-byte file-scope
  * __device__ array of the library instead of a cudaMalloc'd block; every GPU
  * that loads the library holds that array until the process exits.  The
  * call allocates nothing (no cudaMalloc, cudaFree or allocating library
- * routine); it rejects sizes beyond its limits (rows/cols >= 2^31 - 1024, or
- * a kernel scratch larger than the array) with SWCORR_ERR_UNSUPPORTED.
+ * routine); it rejects sizes beyond its limits (rows or cols > 2^31 - 1024,
+ * or a kernel scratch larger than the array) with SWCORR_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
- * shares the array and clears its status words before launching, so calls
- * whose work overlaps on the GPU (different streams, no ordering between
- * them) race on it.  Asynchronous: returns after queuing. */
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the process: after cudaDeviceReset() on a device, do
+ * not use this call on that device again.  Every call shares the array and
+ * clears its status words before launching, so calls whose work overlaps on
+ * the GPU (different streams, no ordering between them) race on it.
+ * Asynchronous: returns after queuing.  Device-side errors (a bounded wait
+ * that gave up, leaving outputs of that work item undefined) are not
+ * reported here: read them with swcorr_noalloc_status. */
 swcorr_status swcorr_run2d_u16_noalloc(int64_t rows, int64_t cols, int32_t kh, int32_t kw, const void* x,
                                        const void* y, int64_t in_pitch, float* c, int64_t out_pitch,
                                        void* stream);
+
+/* Status of the no-allocation runs queued on `stream` since the last call:
+ * waits for the stream, copies the status words out of the static array
+ * (into host memory on the call's stack; nothing is allocated), clears them,
+ * and returns SWCORR_ERR_TIMEOUT if a kernel's bounded wait gave up, else
+ * SWCORR_OK.  *fallbacks (if not NULL) receives the number of windows the
+ * kernel recomputed through its exact per-window path (-1 on error).  The
+ * paper has no counterpart. */
+swcorr_status swcorr_noalloc_status(void* stream, int64_t* fallbacks);
 
 /* Number of output windows the plan computes per run. */
 int64_t swcorr_plan_outputs(swcorr_plan p);

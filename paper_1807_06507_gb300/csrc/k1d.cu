@@ -1,5 +1,6 @@
 // k1d.cu -- launch of the fused 1-D correlation kernel.
 #include "k1d.cuh"
+#include "devonce.h"
 #include "launch.h"
 
 namespace swc {
@@ -10,13 +11,11 @@ int k1d_outputs_per_lane() { return kM1; }
 
 template <bool F32, bool UNIT>
 static cudaError_t launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k1d_kernel<kM1, F32, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device
+  cudaError_t e = once_per_device(attr_done, [] {
+    return cudaFuncSetAttribute(k1d_kernel<kM1, F32, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   k1d_kernel<kM1, F32, UNIT><<<grid, 32 * warps, smem, st>>>(p);
   return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // k2d_f32.cu -- kernel entry points and instantiations of the fused 2-D
 // float32 correlation (one warp per CTA, persistent over work items).
 #include "k2d_f32.cuh"
+#include "devonce.h"
 #include "launch.h"
 
 namespace swc {
@@ -46,13 +47,11 @@ __global__ void __launch_bounds__(32, 12) k2d_f32_kernel(const __grid_constant__
 
 template <int M, int KW, bool TMA>
 static cudaError_t launch_t(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k2d_f32_kernel<M, KW, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device
+  cudaError_t e = once_per_device(attr_done, [] {
+    return cudaFuncSetAttribute(k2d_f32_kernel<M, KW, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   k2d_f32_kernel<M, KW, TMA><<<grid, 32, smem, st>>>(p);
   return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // k2d_u16w.cu -- instantiations of the fused 2-D uint16 kernel with 64-bit
 // second-moment sums (large windows).
 #include "k2d_u16.cuh"
+#include "devonce.h"
 #include "launch.h"
 
 namespace swc {
@@ -9,13 +10,11 @@ namespace swc {
 
 template <int M, int KW, bool TMA>
 static cudaError_t launch_tma(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
-  static bool attr_done = false;  // per-process; harmless to repeat
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device
+  cudaError_t e = once_per_device(attr_done, [] {
+    return cudaFuncSetAttribute(k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   k2d_u16_kernel<M, KW, TMA, SWC_K2D_WIDE><<<grid, 32, smem, st>>>(p);
   return cudaGetLastError();
 }

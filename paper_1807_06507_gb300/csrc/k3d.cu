@@ -1,5 +1,6 @@
 // k3d.cu -- instantiations and launch of the fused 3-D correlation kernel.
 #include "k3d.cuh"
+#include "devonce.h"
 #include "launch.h"
 
 namespace swc {
@@ -16,13 +17,11 @@ constexpr int tx3() {
 
 template <int K>
 static cudaError_t launch_k(const K3DParams& p, int grid, size_t smem, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device
+  cudaError_t e = once_per_device(attr_done, [] {
+    return cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   k3d_kernel<kTY3, tx3<K>(), K, K><<<grid, K3_THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }

@@ -33,7 +33,9 @@ uint32_t* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is taken
-// once per device with that device current.
+// once per device with that device current.  The cached address belongs to
+// the device's primary context: after cudaDeviceReset() on a device this
+// entry point must not be used on that device again in the same process.
 swcorr_status scratch_address(int dev, uint32_t** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(SWCORR_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -62,6 +64,7 @@ extern "C" swcorr_status swcorr_run2d_u16_noalloc(int64_t rows, int64_t cols, in
   if (ip < cols || op < cols) return fail(SWCORR_ERR_INVALID_ARG, "pitches must be >= cols");
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 1)
     return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
+  if (reinterpret_cast<uintptr_t>(c) & 3) return fail(SWCORR_ERR_ALIGNMENT, "c must be 4-byte aligned");
   if (ST_WORDS > SWCORR_NOALLOC_SCRATCH_WORDS)
     return fail(SWCORR_ERR_UNSUPPORTED, "kernel scratch of %d words exceeds the %d-word static array", (int)ST_WORDS,
                 SWCORR_NOALLOC_SCRATCH_WORDS);
@@ -89,5 +92,28 @@ extern "C" swcorr_status swcorr_run2d_u16_noalloc(int64_t rows, int64_t cols, in
   if (e != cudaSuccess) return cuda_fail(e, "clear no-alloc scratch");
   e = k2d_u16_launch(kw, k2, grid, smem, s, use_tma);
   if (e != cudaSuccess) return cuda_fail(e, "2-D uint16 kernel launch");
+  return SWCORR_OK;
+}
+
+// The kernel latches its errors (a bounded wait that gave up) and counts its
+// exact per-window recomputations in the static array; nothing else can see
+// them, so this call copies the words out (into a host array on the stack:
+// no allocation), waits for the stream and clears them for the next call.
+extern "C" swcorr_status swcorr_noalloc_status(void* stream, int64_t* fallbacks) {
+  if (fallbacks) *fallbacks = -1;
+  DeviceInfo dev;
+  swcorr_status st = device_info(&dev);
+  if (st != SWCORR_OK) return st;
+  uint32_t* scratch = nullptr;
+  if ((st = scratch_address(dev.dev, &scratch)) != SWCORR_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t h[ST_WORDS];
+  cudaError_t e = cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(h), s);
+  if (e != cudaSuccess) return cuda_fail(e, "read no-alloc status words");
+  if (fallbacks) *fallbacks = h[ST_FALLBACK];
+  if (h[ST_ERROR] & ERRBIT_TIMEOUT) return fail(SWCORR_ERR_TIMEOUT, "a kernel's bounded wait gave up");
+  if (h[ST_ERROR]) return fail(SWCORR_ERR_CUDA, "device status bits 0x%x", h[ST_ERROR]);
   return SWCORR_OK;
 }

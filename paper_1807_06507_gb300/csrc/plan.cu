@@ -667,6 +667,8 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   if (!p) return fail(SWCORR_ERR_INVALID_ARG, "plan is NULL");
   if (p->kind == KIND_BATCHED) return fail(SWCORR_ERR_INVALID_ARG, "batched plans run with swcorr_run_batched");
   if (!x || !y || !c) return fail(SWCORR_ERR_INVALID_ARG, "x, y and c must not be NULL");
+  if (reinterpret_cast<uintptr_t>(c) & 3) return fail(SWCORR_ERR_ALIGNMENT, "c must be 4-byte aligned");
+  if (reinterpret_cast<uintptr_t>(sums) & 7) return fail(SWCORR_ERR_ALIGNMENT, "sums must be 8-byte aligned");
   if ((p->flags & SWCORR_FLAG_EMIT_SUMS) && !sums)
     return fail(SWCORR_ERR_INVALID_ARG, "plan has SWCORR_FLAG_EMIT_SUMS: sums must not be NULL");
   if (!(p->flags & SWCORR_FLAG_EMIT_SUMS)) sums = nullptr;

@@ -25,7 +25,7 @@ EXPORTS = ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune",
            "swcorr_tune_lookup", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",
            "swcorr_run_batched", "swcorr_plan_status", "swcorr_plan_fallbacks", "swcorr_plan_outputs",
            "swcorr_plan_destroy", "swcorr_status_string", "swcorr_last_error", "swcorr_version",
-           "swcorr_run2d_u16_noalloc")
+           "swcorr_run2d_u16_noalloc", "swcorr_noalloc_status")
 
 # Tune cache shipped with the package (written by autotune.py); used unless
 # SWCORR_TUNE_FILE names another file.
@@ -109,6 +109,8 @@ def load(path: str | None = None):
         lib.swcorr_run2d_u16_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp,
                                                  vp, ctypes.c_int64, vp, ctypes.c_int64, vp]
         lib.swcorr_run2d_u16_noalloc.restype = ctypes.c_int
+        lib.swcorr_noalloc_status.argtypes = [vp, i64p]
+        lib.swcorr_noalloc_status.restype = ctypes.c_int
         lib.swcorr_status_string.argtypes = [ctypes.c_int]
         lib.swcorr_status_string.restype = ctypes.c_char_p
         lib.swcorr_last_error.restype = ctypes.c_char_p
