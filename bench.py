@@ -212,10 +212,13 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
     xf, yf = vis.astype(np.float32), ir.astype(np.float32)
     p = swcorr.Plan(xf.shape, K, dtype="f32")
     sets = [(to(xf), to(yf), torch.empty(xf.shape, dtype=torch.float32, device=dev)) for _ in range(3)]
+    p.fallbacks()
     t = _events_time(torch, lambda i: p.run(*sets[i % 3][:2], c=sets[i % 3][2]), 30)
     p.check_status()
+    fb = p.fallbacks() / 32.0
     idx = rng.integers(0, xf.size, 100_000)
     out["night_f32_3000x4000_k7"] = {"windows_per_s": xf.size / t, "us_per_launch": t * 1e6,
+                                      "recomputed_windows_per_launch": fb,
                                       "gbs_algorithmic": xf.size * BYTES_PER_WINDOW_F32 / t / 1e9,
                                       **_scored_dc(sets[0][2].cpu().numpy(), xf, yf, K, None, idx)}
     del sets, p
@@ -225,10 +228,13 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
     p = swcorr.Plan(x1.shape, 1001, dtype="f32")
     xd, yd = to(x1), to(y1)
     c1 = torch.empty(x1.shape, dtype=torch.float32, device=dev)
+    p.fallbacks()
     t = _events_time(torch, lambda i: p.run(xd, yd, c=c1), 10)
     p.check_status()
+    fb = p.fallbacks() / 12.0
     idx = np.unique(np.r_[rng.integers(0, x1.size, 100_000), np.arange(2000), x1.size - 1 - np.arange(2000)])
     out["walk_1d_2^26_k1001"] = {"windows_per_s": x1.size / t, "us_per_launch": t * 1e6,
+                                 "recomputed_windows_per_launch": fb,
                                  "gbs_algorithmic": x1.size * BYTES_PER_WINDOW_F32 / t / 1e9,
                                  **_scored_dc(c1.cpu().numpy(), x1, y1, 1001, None, idx)}
     del xd, yd, c1, p, x1, y1
@@ -239,12 +245,15 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
     for st, bpw in ((1, BYTES_PER_WINDOW_F32), (2, 8 * 8 + 4)):
         p = swcorr.Plan(x3.shape, 9, st, dtype="f32")
         c3 = torch.empty(p.oshape, dtype=torch.float32, device=dev)
+        p.fallbacks()
         t = _events_time(torch, lambda i: p.run(xd, yd, c=c3), 10)
         p.check_status()
+        fb = p.fallbacks() / 12.0
         nout = int(np.prod(p.oshape))
         idx = rng.integers(0, nout, 50_000)
         out[f"halfspace_3d_256x512x512_k9_s{st}"] = {
             "windows_per_s": nout / t, "us_per_launch": t * 1e6, "gbs_algorithmic": nout * bpw / t / 1e9,
+            "recomputed_windows_per_launch": fb,
             **_scored_dc(c3.cpu().numpy(), x3, y3, 9, st, idx)}
         del c3, p
     del xd, yd, x3, y3

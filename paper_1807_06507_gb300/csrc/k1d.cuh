@@ -10,10 +10,11 @@
 //    shared memory with 1-D TMA boxes issued by many threads at once; cells
 //    before the start or past the end of the series read as 0.
 //  * Values become exact integers: uint16 as they are (read in place);
-//    float32 through a fixed-point map of the chunk (reference at the
-//    midpoint of the chunk's range, power-of-two scale, |X| <= 2^qbits with
-//    n 2^qbits < 2^31), converted in place four cells per access.  Cells off
-//    the series become 0.
+//    float32 through a fixed-point map of the chunk (fxmap.cuh: reference on
+//    the grid near the midpoint of the chunk's range, power-of-two scale,
+//    |X| < 2^qbits with n 2^qbits < 2^31), converted in place four cells per
+//    access, noting whether every value converted without rounding.  Cells
+//    off the series become 0.
 //  * Lane j of warp w owns M1 consecutive outputs.  The warp's span is cut
 //    into segments of M1*stride cells, so lane j's first window starts at
 //    segment j: q whole segments plus the first r cells of the next
@@ -27,11 +28,18 @@
 //    int64 for each output (NaN for a zero variance).  The lane's results
 //    stay in registers until the whole CTA is done with the span, which then
 //    stages them for coalesced stores.
+//  * float32 certificate (fxmap.cuh): a window passes when
+//    vx, vy >= (rho n / 4.5e-6)^2 (rho = 0 for a channel whose chunk
+//    converted exactly).  A lane with failing windows recomputes them after
+//    the stores with a map of its own span at up to 24 bits (64-bit sums,
+//    sliding from window to window); a window that still fails is recomputed
+//    from its own cells (fx_recompute).
 #pragma once
 
 #include <type_traits>
 
 #include "common.cuh"
+#include "fxmap.cuh"
 #include "kparams.h"
 #include "k1d_params.h"
 
@@ -88,35 +96,93 @@ struct Sums5 {
 };
 
 // Eq. 2 from exact modular window sums (the results fit in int64; the first
-// moments are below 2^31 in magnitude).
-__device__ __forceinline__ float pearson_exact(const Sums5& s, uint32_t n) {
+// moments are below 2^31 in magnitude).  fail: the float32 certificate's
+// quick test (vx >= Kx, vy >= Ky) did not pass.
+__device__ __forceinline__ float pearson_exact(const Sums5& s, uint32_t n, float Kx, float Ky, bool& fail) {
   const long long sx = (int)s.x, sy = (int)s.y;
   const long long vx = (long long)((uint64_t)n * s.xx - (uint64_t)(sx * sx));
   const long long vy = (long long)((uint64_t)n * s.yy - (uint64_t)(sy * sy));
   const long long num = (long long)((uint64_t)n * s.xy - (uint64_t)(sx * sy));
+  const float fvx = i64_to_f32(vx), fvy = i64_to_f32(vy);
+  fail = !(fvx >= Kx && fvy >= Ky);
   // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
-  return clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
+  return clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
 }
 
-// Fixed-point map of a float32 chunk: m = midpoint of [lo, hi], scale 2^e
-// with |x - m| 2^e <= 2^qbits.
-__device__ __forceinline__ void fixed_point(float lo, float hi, int qbits, float& m, float& s) {
-  if (!(lo <= hi)) lo = hi = 0.0f;  // a chunk with no cell on the series
-  m = lo + 0.5f * (hi - lo);
-  const float A = fmaxf(hi - m, m - lo);
-  int e = 0;
-  if (A > 0.0f) {
-    int ea;
-    frexpf(A, &ea);  // A < 2^ea
-    e = min(max(qbits - ea, -126), 126);
+// Recompute the failing outputs (bits of `fail`) of one lane whose first
+// output is j_base, from the chunk's float32 span in shared memory (cell i of
+// the series at gx[i - e0]): a fixed-point map of the lane's own span
+// (fx_wide: up to 26 bits, exact for values on the grid, else within 1/2),
+// 64-bit window sums slid from one failing window to the next, Eq. 2 in
+// 128-bit integers, the certificate;
+// windows that still fail are recomputed from their cells.  Writes out[j]
+// directly and counts every recomputed window.
+static __device__ __noinline__ void lane_redo_1d(const float* sx_span, const float* sy_span, long long e0,
+                                                 long long N, int k, int h1, int h2, int stride, long long j_base,
+                                                 uint64_t fail, long long n_out, float* out, uint32_t* status) {
+  const float* gx = sx_span - e0;  // indexed by series cell (every cell used lies in the span)
+  const float* gy = sy_span - e0;
+  const int ta = __ffsll((long long)fail) - 1, tb = 63 - __clzll((long long)fail);
+  const long long a = max(0ll, (j_base + ta) * stride - h1), b = min(N - 1, (j_base + tb) * stride + h2);
+  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+  for (long long i = a; i <= b; i++) {
+    const float u = gx[i], v = gy[i];
+    xlo = fminf(xlo, u); xhi = fmaxf(xhi, u); ylo = fminf(ylo, v); yhi = fmaxf(yhi, v);
   }
-  s = __int_as_float((127 + e) << 23);
-}
-
-// Round to nearest of (v - m) * s (|result| <= 2^22) through the float32
-// significand: adding 1.5 * 2^23 puts the integer in the low mantissa bits.
-__device__ __forceinline__ int to_fixed(float v, float m, float s) {
-  return __float_as_int(fmaf(v - m, s, 12582912.0f)) - 0x4B400000;
+  if (xlo == xhi || ylo == yhi) {  // a channel whose span is one value: every window is constant
+    uint32_t count = 0;
+    for (int t = ta; t <= tb; t++)
+      if (((fail >> t) & 1ull) && j_base + t < n_out) {
+        out[j_base + t] = __int_as_float(0x7fc00000);
+        count++;
+      }
+    if (count) atomicAdd(status + ST_FALLBACK, count);
+    return;
+  }
+  const FxWide wx = fx_wide(xlo, xhi, k), wy = fx_wide(ylo, yhi, k);
+  long long Sx = 0, Sy = 0, Sxx = 0, Syy = 0, Sxy = 0;
+  bool gx_ok = true, gy_ok = true;  // every value read so far on its channel's grid
+  auto cell = [&](long long i, int sign) {
+    const long long X = fx_wide_quant(gx[i], wx, gx_ok), Y = fx_wide_quant(gy[i], wy, gy_ok);
+    Sx += sign * X; Sy += sign * Y; Sxx += sign * (X * X); Syy += sign * (Y * Y); Sxy += sign * (X * Y);
+  };
+  long long lo = 0, hi = -1;  // cells currently summed
+  uint32_t count = 0;
+  for (int t = ta; t <= tb; t++) {
+    if (!((fail >> t) & 1ull)) continue;
+    const long long j = j_base + t;
+    if (j >= n_out) break;
+    const long long nlo = max(0ll, j * stride - h1), nhi = min(N - 1, j * stride + h2);
+    if (nlo > hi) {  // no overlap with the previous window: start again
+      Sx = Sy = Sxx = Syy = Sxy = 0;
+      for (long long i = nlo; i <= nhi; i++) cell(i, 1);
+    } else {
+      for (long long i = lo; i < nlo; i++) cell(i, -1);
+      for (long long i = hi + 1; i <= nhi; i++) cell(i, 1);
+    }
+    lo = nlo;
+    hi = nhi;
+    const long long n = nhi - nlo + 1;
+    const __int128 vx = (__int128)n * Sxx - (__int128)Sx * Sx;
+    const __int128 vy = (__int128)n * Syy - (__int128)Sy * Sy;
+    const __int128 num = (__int128)n * Sxy - (__int128)Sx * Sy;
+    float c;
+    if (fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, gx_ok ? 0.0f : 0.5f, gy_ok ? 0.0f : 0.5f)) {
+      c = fx_pearson128(num, vx, vy);  // exact zero variance: NaN
+    } else {
+      FxBox bx;
+      bx.gx = sx_span;
+      bx.gy = sy_span;
+      bx.pz = bx.py = 0;
+      bx.z0 = bx.z1 = bx.y0 = bx.y1 = 0;
+      bx.x0 = (int)(nlo - e0);
+      bx.x1 = (int)(nhi - e0);
+      if (!fx_box_exact(bx, &c)) c = fx_box_fp64(bx);
+    }
+    out[j] = c;
+    count++;
+  }
+  if (count) atomicAdd(status + ST_FALLBACK, count);
 }
 
 template <int M1, bool F32, bool UNIT>
@@ -162,27 +228,32 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     const int v_hi = (int)max(0ll, min((long long)ncell, p.N - e0));
 
     // ---- load the span
-    if (p.gx == nullptr) {
-      if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * ncell * sizeof(T)));
-      __syncthreads();
-      for (int b = tid; b < 2 * p.nbox; b += blockDim.x) {
-        const bool ych = b >= p.nbox;
-        const int bb = ych ? b - p.nbox : b;
-        fence_proxy_async_smem();
-        tma_load_1d((ych ? Y : X) + (size_t)bb * 256, ych ? &p.tmy : &p.tmx, (int)(e0 + 256ll * bb), bar);
+    auto load_span = [&]() -> bool {
+      if (p.gx == nullptr) {
+        if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * ncell * sizeof(T)));
+        __syncthreads();
+        for (int b = tid; b < 2 * p.nbox; b += blockDim.x) {
+          const bool ych = b >= p.nbox;
+          const int bb = ych ? b - p.nbox : b;
+          fence_proxy_async_smem();
+          tma_load_1d((ych ? Y : X) + (size_t)bb * 256, ych ? &p.tmy : &p.tmx, (int)(e0 + 256ll * bb), bar);
+        }
+        if (!mbar_wait_bounded(bar, phase, p.status)) return false;
+        phase ^= 1u;
+      } else {
+        for (int e = tid; e < ncell; e += blockDim.x) {
+          const bool ok = e >= v_lo && e < v_hi;
+          X[e] = ok ? reinterpret_cast<const T*>(p.gx)[e0 + e] : (T)0;
+          Y[e] = ok ? reinterpret_cast<const T*>(p.gy)[e0 + e] : (T)0;
+        }
+        __syncthreads();
       }
-      if (!mbar_wait_bounded(bar, phase, p.status)) return;
-      phase ^= 1u;
-    } else {
-      for (int e = tid; e < ncell; e += blockDim.x) {
-        const bool ok = e >= v_lo && e < v_hi;
-        X[e] = ok ? reinterpret_cast<const T*>(p.gx)[e0 + e] : (T)0;
-        Y[e] = ok ? reinterpret_cast<const T*>(p.gy)[e0 + e] : (T)0;
-      }
-      __syncthreads();
-    }
+      return true;
+    };
+    if (!load_span()) return;
 
     // ---- float32: fixed point of the chunk, converted in place
+    float Kx = 0.0f, Ky = 0.0f;  // certificate thresholds (0: exact, or uint16)
     if constexpr (F32) {
       float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
       const float4* X4 = reinterpret_cast<const float4*>(X);
@@ -228,26 +299,41 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
         ylo = fminf(ylo, red[2 * nw + w]);
         yhi = fmaxf(yhi, red[3 * nw + w]);
       }
-      float mx, sx, my, sy;
-      fixed_point(xlo, xhi, p.qbits, mx, sx);
-      fixed_point(ylo, yhi, p.qbits, my, sy);
+      const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
       int4* XW = reinterpret_cast<int4*>(X);
       int4* YW = reinterpret_cast<int4*>(Y);
+      // conversion in place; rx, ry: largest rounding residual of an on-series value
+      float rx = 0.0f, ry = 0.0f;
+      auto cv = [&](float v, const FxMap& q, float& racc, bool on) {
+        const float d = v - q.msub;
+        const float t = fmaf(d, q.s, q.C);
+        const float r = fmaf(d, q.s, -(t - q.C));  // the conversion's rounding, exactly
+        racc = on ? fmaxf(racc, fabsf(r)) : racc;
+        return on ? __float_as_int(t) - 0x4B400000 : 0;
+      };
       for (int v = tid; v < ncell / 4; v += blockDim.x) {
         const int e = 4 * v;
         const float4 a = X4[v], b = Y4[v];
-        int4 ia = make_int4(to_fixed(a.x, mx, sx), to_fixed(a.y, mx, sx), to_fixed(a.z, mx, sx), to_fixed(a.w, mx, sx));
-        int4 ib = make_int4(to_fixed(b.x, my, sy), to_fixed(b.y, my, sy), to_fixed(b.z, my, sy), to_fixed(b.w, my, sy));
-        if (!(e >= v_lo && e + 4 <= v_hi)) {
-          if (!(e + 0 >= v_lo && e + 0 < v_hi)) ia.x = ib.x = 0;
-          if (!(e + 1 >= v_lo && e + 1 < v_hi)) ia.y = ib.y = 0;
-          if (!(e + 2 >= v_lo && e + 2 < v_hi)) ia.z = ib.z = 0;
-          if (!(e + 3 >= v_lo && e + 3 < v_hi)) ia.w = ib.w = 0;
+        int4 ia, ib;
+        if (e >= v_lo && e + 4 <= v_hi) {
+          ia = make_int4(cv(a.x, qx, rx, true), cv(a.y, qx, rx, true), cv(a.z, qx, rx, true), cv(a.w, qx, rx, true));
+          ib = make_int4(cv(b.x, qy, ry, true), cv(b.y, qy, ry, true), cv(b.z, qy, ry, true), cv(b.w, qy, ry, true));
+        } else {
+          const bool o0 = e >= v_lo && e < v_hi, o1 = e + 1 >= v_lo && e + 1 < v_hi;
+          const bool o2 = e + 2 >= v_lo && e + 2 < v_hi, o3 = e + 3 >= v_lo && e + 3 < v_hi;
+          ia = make_int4(cv(a.x, qx, rx, o0), cv(a.y, qx, rx, o1), cv(a.z, qx, rx, o2), cv(a.w, qx, rx, o3));
+          ib = make_int4(cv(b.x, qy, ry, o0), cv(b.y, qy, ry, o1), cv(b.z, qy, ry, o2), cv(b.w, qy, ry, o3));
         }
         XW[v] = ia;
         YW[v] = ib;
       }
-      __syncthreads();
+      // a channel converts exactly when no value rounded and x - m is exact
+      // (fused form, or one sign within a factor 2: rho = 1/2)
+      const bool inexact_x = __syncthreads_or(rx != 0.0f) || qx.rho != 0.5f;
+      const bool inexact_y = __syncthreads_or(ry != 0.0f) || qy.rho != 0.5f;
+      const float k0 = 4.9432e10f * (float)p.k * (float)p.k;  // (1 / 4.5e-6)^2 * 1.001 * n^2
+      Kx = inexact_x ? k0 * qx.rho * qx.rho : 0.0f;
+      Ky = inexact_y ? k0 * qy.rho * qy.rho : 0.0f;
     }
 
     // ---- this warp's outputs: segment sums, first windows, slide
@@ -311,10 +397,13 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     const int e_out = woff + lane * seg;  // first cell of the lane's first window
     const int e_in = e_out + p.k;         // first cell to enter after it
     float res[M1];
+    uint64_t fail = 0;  // outputs whose certificate's quick test failed
     if constexpr (UNIT) {  // stride 1
 #pragma unroll
       for (int t = 0; t < M1; t++) {
-        res[t] = pearson_exact(W, n_of(j_base + t));
+        bool f;
+        res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
+        fail |= (uint64_t)f << t;
         if (t + 1 < M1) {
           const int ei = e_in + t, eo = e_out + t;
           const bool in_ok = ei < ncell;
@@ -324,7 +413,9 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     } else {
 #pragma unroll
       for (int t = 0; t < M1; t++) {
-        res[t] = pearson_exact(W, n_of(j_base + t));
+        bool f;
+        res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
+        fail |= (uint64_t)f << t;
         if (t + 1 < M1) {
           for (int u = 0; u < p.stride; u++) {
             const int ei = e_in + t * p.stride + u, eo = e_out + t * p.stride + u;
@@ -351,6 +442,16 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
       }
     } else {
       for (int u = lane; u < nvalid; u += 32) dst[u] = sw[u];
+    }
+    if constexpr (F32) {
+      // lanes with failing windows recompute them from the chunk's floats,
+      // loaded again into the span buffer once every warp has stored
+      if (__syncthreads_or(fail != 0ull)) {
+        if (!load_span()) return;
+        if (fail)
+          lane_redo_1d(reinterpret_cast<const float*>(X), reinterpret_cast<const float*>(Y), e0, p.N, p.k, p.h1, p.h2,
+                       p.stride, j_base, fail, p.n_out, p.out, p.status);
+      }
     }
     __syncthreads();  // the span is reused by the next chunk
   }

@@ -20,8 +20,10 @@ struct K1DParams {
   int nseg;          // segments of M1*stride cells a warp sums (<= 64)
   int is_f32;
   int qbits;         // float32 fixed-point magnitude bits
-  const void* gx;    // plain-load fallback (unaligned bases)
+  const void* gx;    // plain-load fallback (unaligned bases); NULL when TMA loads
   const void* gy;
+  const void* rx;    // the series themselves (always set: float32 windows that
+  const void* ry;    //   fail their certificate are recomputed from them)
   float* out;
   uint32_t* status;
 };

@@ -7,7 +7,10 @@
 namespace swc {
 
 template <int M, int KW, bool TMA>
-__global__ void __launch_bounds__(32, 12) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
+#ifndef SWC_K2DF_MINB
+#define SWC_K2DF_MINB 12  // resident one-warp CTAs per SM the float32 2-D kernel is compiled for
+#endif
+__global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
   using G = Geo2DF<M, KW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring2DF rg;

@@ -10,28 +10,38 @@
 //
 //  * Pass 1 streams the item's rows through the ring once and takes, per
 //    lane, the range [lo, hi] of x and of y over the lane's columns.
-//  * Each value becomes X = round((x - m) * 2^e), m the midpoint of [lo, hi]
-//    and 2^e the largest power of two with |x - m| * 2^e < 2^q, q = 22 when
-//    the window has at most 512 cells and 21 above (so that n^2 (2^q)^2, the
-//    bound of n Sxx - Sx^2, stays below 2^63).  x - m is one FADD (exact near m); one FFMA with the
-//    constant 1.5 * 2^23 rounds to the integer, one IADD extracts it.  The
-//    affine map is the same for every window of the lane, so it leaves
-//    Pearson's c unchanged; the rounding is the only error, at most
-//    2^-(q+1) * max|x - m| per value.
-//  * Cells outside the grid must add nothing.  Rows outside the grid (and the
-//    missing leaving row of the first kh-1 rows) are mapped to exactly 0 by a
-//    per-row switch of the scale to 0.  Columns outside the grid, which
-//    only a few border lanes see, enter as the constant G = X(0); since the
-//    sums are exact modular integers, step 4 subtracts their known count times
-//    G, G^2 and Gx*Gy exactly.
+//  * Each value becomes X = round((x - m) s) with s = 2^e and m on the 2^-e
+//    grid (fxmap.cuh), |X| < 2^q, q = 22 when the window has at most 511
+//    cells and fewer above (n 2^q < 2^31 keeps the first-moment sums in
+//    int32).  The affine map is the same for every window of the lane, so it
+//    leaves Pearson's c unchanged; the rounding of each value is the only
+//    error.
+//  * Cells outside the grid must add nothing.  They are read as 0 (TMA zero
+//    fill).  The lane's map has the subtract form (fxmap.cuh), and rows
+//    outside the grid switch its reference to 0, which converts their zero
+//    fill to exactly X = 0 (the missing leaving row of the first kh-1 rows
+//    enters as 0 directly).  Columns outside the
+//    grid, which only a few border lanes see, enter as the constant
+//    G = X(0); since the sums are exact modular integers, step 4 subtracts
+//    their known count times G, G^2 and Gx*Gy exactly.  (An off-grid column
+//    is off-grid in the entering and the leaving row alike, so its entering-
+//    minus-leaving differences are 0 or +-G and the products stay exact.)
 //  * Pass 2 is the D-march with int32 first-moment and int64 second-moment
 //    sums, all exact; step 4 evaluates n Sxy - Sx Sy etc. exactly in int64 and
 //    rounds once to float32 per factor.  A zero variance gives NaN exactly.
+//  * Each window's result is certified (fxmap.cuh): with rho the lane's
+//    rounding bound, |dc| <= rho n (1/sqrt(vx) + 1/sqrt(vy)) + 7e-7.  The
+//    common case passes a one-comparison-per-channel test.  When a window of
+//    some lane does not, the whole warp determines, once per item, which of
+//    its lanes convert exactly (rho = 0, every window certified); a failing
+//    window of an inexact lane is recomputed from its own cells and stored
+//    over the fixed-point result.
 #pragma once
 
 #include <type_traits>
 
 #include "common.cuh"
+#include "fxmap.cuh"
 #include "kparams.h"
 
 namespace swc {
@@ -64,31 +74,66 @@ struct Ring2DF {
   int PF;
 };
 
-// Fixed-point map of one channel of one lane (see the file header).
-struct Quant {
-  float m;  // reference (midpoint of the lane's range)
-  float s;  // 2^e; 0 maps every value to X = 0 (rows outside the grid)
+// Fix-up of one output row of a lane: every window flagged in `fail`
+// (bit c: centre column cl + c) is recomputed from its own cells
+// (fx_recompute) and stored over the fixed-point result.
+struct FixScene2D {  // the fields of a scene the fix-up reads (passed by value)
+  const float* gx;
+  const float* gy;
+  long long in_pitch;
+  int H, W, h1, h2, kw, sx;
 };
 
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
-
-__device__ __forceinline__ int quant(float x, const Quant& q) {
-  return __float_as_int(fmaf(x - q.m, q.s, kMagic)) - 0x4B400000;
+// Whether every in-grid value of a lane's item (rows [r0, r1), the lane's
+// NCOL columns from c0, those with index in [e_lo, e_hi) inside the grid)
+// converts without rounding under the lane's maps.  Integer data on a grid
+// step of at most 1 passes a cheap first test (x - m and (x - m) s are then
+// exact); otherwise every value is tested (fx_on_grid).  Each row's loads
+// are independent, so they are in flight together.
+template <int NCOL>
+static __device__ __noinline__ bool lane_exact_2d(const float* gx, const float* gy, long long pitch, int r0, int r1,
+                                                  int c0, int e_lo, int e_hi, FxMap qx, FxMap qy) {
+  for (int pass = (qx.s >= 1.0f && qy.s >= 1.0f) ? 0 : 1; pass < 2; pass++) {
+    bool ok = true;
+    for (int r = r0; r < r1; r++) {
+      const long long o = (long long)r * pitch + c0;
+      float vx[NCOL], vy[NCOL];
+#pragma unroll
+      for (int e = 0; e < NCOL; e++) {
+        vx[e] = (e >= e_lo && e < e_hi) ? gx[o + e] : 0.0f;
+        vy[e] = (e >= e_lo && e < e_hi) ? gy[o + e] : 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < NCOL; e++) {
+        if (pass == 0)
+          ok = ok && vx[e] == rintf(vx[e]) && vy[e] == rintf(vy[e]);
+        else if (e >= e_lo && e < e_hi)
+          ok = ok && fx_on_grid(vx[e], qx) && fx_on_grid(vy[e], qy);
+      }
+    }
+    if (ok) return true;
+  }
+  return false;
 }
 
-__device__ __forceinline__ Quant make_quant(float lo, float hi, int qbits) {
-  if (!(lo <= hi)) lo = hi = 0.0f;  // a lane with no in-grid cell
-  Quant q;
-  q.m = lo + 0.5f * (hi - lo);
-  const float A = fmaxf(hi - q.m, q.m - lo);  // max |x - m|
-  int e = 0;
-  if (A > 0.0f) {
-    int ea;
-    frexpf(A, &ea);  // A < 2^ea
-    e = min(max(qbits - ea, -126), 126);
+static __device__ __noinline__ void fixup_row_2d(FixScene2D sc, uint32_t fail, int rc, int cl, float* orow,
+                                                 uint32_t* status) {
+  const int w1 = (sc.kw - 1) / 2, w2 = sc.kw / 2;
+  for (; fail; fail &= fail - 1) {
+    const int cc = cl + (__ffs(fail) - 1);
+    if (cc >= sc.W || (sc.sx != 1 && cc % sc.sx != 0)) continue;
+    FxBox b;
+    b.gx = sc.gx;
+    b.gy = sc.gy;
+    b.pz = 0;
+    b.py = sc.in_pitch;
+    b.z0 = b.z1 = 0;
+    b.y0 = max(rc - sc.h1, 0);
+    b.y1 = min(rc + sc.h2, sc.H - 1);
+    b.x0 = max(cc - w1, 0);
+    b.x1 = min(cc + w2, sc.W - 1);
+    orow[sc.sx == 1 ? cc : cc / sc.sx] = fx_recompute(b, status);
   }
-  q.s = __int_as_float((127 + e) << 23);
-  return q;
 }
 
 template <int M, int KW, bool TMA>
@@ -219,10 +264,22 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
       }))
     return false;
 
-  const Quant qx = make_quant(xlo, xhi, sc.qbits), qy = make_quant(ylo, yhi, sc.qbits);
-  Quant qxe = qx, qye = qy, qxl = qx, qyl = qy;  // per-row maps (exact zero off the grid)
+  // subtract form (C = 1.5*2^23): rows outside the grid take the reference 0,
+  // which converts their zero fill to X = 0
+  const FxMap qx = fx_make(xlo, xhi, sc.qbits, false), qy = fx_make(ylo, yhi, sc.qbits, false);
+  float mxe = qx.msub, mye = qy.msub, mxl = qx.msub, myl = qy.msub;  // per-row references
   const bool lane_border = (cl - G::W1 < 0) || (cl + M - 1 + G::W2 > sc.W - 1);
-  const int Gx = quant(0.0f, qx), Gy = quant(0.0f, qy);  // value of an off-grid column
+  const int Gx = fx_quant(0.0f, qx), Gy = fx_quant(0.0f, qy);  // value of an off-grid column
+  // quick certificate: vx >= (rho n / 4.5e-6)^2 with n the interior count
+  // (border windows have fewer cells, so the test is conservative there)
+  int exact_state = -1;  // lane exactness: -1 not yet known, 0 no, 1 yes
+  float Kx, Ky;
+  {
+    const float nmax = (float)(sc.kh * KW);
+    const float k0 = 4.9432e10f * nmax * nmax;  // (1 / 4.5e-6)^2 * 1.001
+    Kx = k0 * qx.rho * qx.rho;
+    Ky = k0 * qy.rho * qy.rho;
+  }
 
   const bool fast_cols = sc.sx == 1 && sc.vec_store;
   uint32_t n_c[M];
@@ -246,17 +303,17 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   // ---- pass 2: the D-march on fixed-point values
   const bool ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
     constexpr bool has_leave = decltype(leave_tag)::value;
+    const int te = t0 + i, tl = te - sc.kh;
+    const bool e_ok = te >= 0 && te < sc.H;
+    const bool l_ok = has_leave && tl >= 0 && tl < sc.H;
+    mxe = e_ok ? qx.msub : 0.0f;
+    mye = e_ok ? qy.msub : 0.0f;
+    mxl = l_ok ? qx.msub : 0.0f;
+    myl = l_ok ? qy.msub : 0.0f;
     const float* pxe = lane_ptr(rg.rx, s);
     const float* pye = lane_ptr(rg.ry, s);
     const float* pxl = lane_ptr(rg.lx, s);
     const float* pyl = lane_ptr(rg.ly, s);
-    const int te = t0 + i, tl = te - sc.kh;
-    const bool e_ok = te >= 0 && te < sc.H;
-    const bool l_ok = has_leave && tl >= 0 && tl < sc.H;
-    qxe.s = e_ok ? qx.s : 0.0f;  // off-grid rows map to X = 0
-    qye.s = e_ok ? qy.s : 0.0f;
-    qxl.s = l_ok ? qx.s : 0.0f;  // so does the missing leaving row of warm-up
-    qyl.s = l_ok ? qy.s : 0.0f;
     uint32_t P0 = 0u, P1 = 0u;
     uint64_t P2 = 0ull, P3 = 0ull, P4 = 0ull;
     uint32_t Ps0[M], Ps1[M];
@@ -276,8 +333,8 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
       for (int u = 0; u < 4; u++) {
         const int e = 4 * h + u - G::E0;
         if (e < 0 || e >= G::NCOL) continue;
-        const int Xe = quant(xa[u], qxe), Xl = has_leave ? quant(xla[u], qxl) : 0;
-        const int Ye = quant(ya[u], qye), Yl = has_leave ? quant(yla[u], qyl) : 0;
+        const int Xe = fx_quant_sub(xa[u], mxe, qx.s), Xl = has_leave ? fx_quant_sub(xla[u], mxl, qx.s) : 0;
+        const int Ye = fx_quant_sub(ya[u], mye, qy.s), Yl = has_leave ? fx_quant_sub(yla[u], myl, qy.s) : 0;
         const int D = (int)((uint32_t)Xe - (uint32_t)Xl), S = (int)((uint32_t)Xe + (uint32_t)Xl);
         const int Dy = (int)((uint32_t)Ye - (uint32_t)Yl), Sy = (int)((uint32_t)Ye + (uint32_t)Yl);
         P0 += (uint32_t)D;
@@ -317,6 +374,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         }
       }
       float res[M];
+      uint32_t fail = 0;  // windows whose quick certificate test failed
 #pragma unroll
       for (int c = 0; c < M; c++) {
         const uint64_t n = cnt_r == sc.kh ? (uint64_t)n_c[c] : (uint64_t)(n_c[c] / sc.kh * cnt_r);
@@ -325,8 +383,10 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         const long long vx = (long long)(n * V2[c] - s0 * s0);
         const long long vy = (long long)(n * V3[c] - s1 * s1);
         const long long num = (long long)(n * V4[c] - s0 * s1);
+        const float fvx = i64_to_f32(vx), fvy = i64_to_f32(vy);
         // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
-        res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
+        res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
+        fail |= (fvx >= Kx && fvy >= Ky) ? 0u : (1u << c);
       }
       if (fast_cols && cl + M <= sc.W) {
 #pragma unroll
@@ -337,6 +397,21 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
           const int cc = cl + c;
           if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) orow[sc.sx == 1 ? cc : cc / sc.sx] = res[c];
         }
+      }
+      // certificate: once per item, when a lane of the warp has a failing
+      // window, every lane learns whether its values convert exactly
+      if (__any_sync(0xffffffffu, fail != 0u && exact_state < 0)) {
+        if (exact_state < 0) {
+          const bool ok = lane_exact_2d<G::NCOL>((const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, max(t0, 0),
+                                                 min(t0 + nrows, sc.H), cl - G::W1, max(0, G::W1 - cl),
+                                                 min(G::NCOL, sc.W - (cl - G::W1)), qx, qy);
+          exact_state = ok ? 1 : 0;
+          if (ok) Kx = Ky = 0.0f;
+        }
+      }
+      if (fail != 0u && exact_state == 0) {
+        const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, KW, sc.sx};
+        fixup_row_2d(fs, fail, rc, cl, orow, status);
       }
       if (lane_border) {
         // restore the running sums for the next rows

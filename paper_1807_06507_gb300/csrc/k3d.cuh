@@ -10,9 +10,19 @@
 //    (z - (kz-1)/2 - 1) of the footprint's input rectangle into shared memory
 //    with 3-D TMA boxes (zero fill off the volume); the leaving plane comes
 //    back from L2, where it was read kz steps earlier.
-//  * Values become exact integers (uint16 as they are; float32 through one
-//    fixed-point map per work item, taken in a first pass over its planes).
-//    Off-volume cells map to 0.
+//  * Values become exact integers: uint16 as they are (off-volume cells 0);
+//    float32 through one fixed-point map per work item (fxmap.cuh), taken in
+//    a first pass over its planes, with |X| < 2^q, q <= 22 chosen so that the
+//    int64 evaluation of Eq. 2 cannot overflow (n 2^q < 2^31.5 * 1.0156, the
+//    map's 1/64 margin) and a plane's window sums fit in int32.  The window's
+//    sum of X is kept modulo 2^32: it is exact as an int32 whenever
+//    n Sxx < 2^62 (Cauchy-Schwarz: |Sx| <= sqrt(n Sxx) < 2^31); a window
+//    beyond that is treated as one whose certificate fails.  Planes
+//    outside the volume switch the map's reference to m' = (C - 1.5*2^23)/s,
+//    which converts their zero fill to X = 0; off-volume rows and columns of
+//    a plane (read as 0, off-volume in the entering and the leaving plane
+//    alike) enter as the constant G = X(0), and step 4 of a border window
+//    subtracts their count times G, G^2 and Gx*Gy exactly.
 //  * Vertical pass: one thread per input column forms, for every row of the
 //    rectangle, the five entering-minus-leaving streams (x, y, x^2, y^2, xy
 //    differences), their running prefix down the column, and the window sums
@@ -24,11 +34,18 @@
 //    kz x ky x kx window of the current output plane.
 //  * Step 4 (Eq. 2) exactly in int64 once the plane's window is complete.
 // All sums are modular integers (uint32 / uint64), hence exact.
+//  * float32 certificate (fxmap.cuh), evaluated in step 4 from the two
+//    rsqrt factors of c: z = rho n (1/sqrt(vx) + 1/sqrt(vy)) <= 8.99e-6.  A
+//    step in which some window fails asks the whole CTA (once per item)
+//    whether the item's values convert exactly (rho = 0); if not, the
+//    failing windows are recomputed from their cells (fx_recompute) and
+//    stored over the fixed-point results.
 #pragma once
 
 #include <type_traits>
 
 #include "common.cuh"
+#include "fxmap.cuh"
 #include "kparams.h"
 
 namespace swc {
@@ -73,8 +90,68 @@ struct Geo3D {
   static_assert(TX % 8 == 0 && TX <= 128, "footprint width must be a multiple of 8 of at most 128");
 };
 
+// Item exactness: 0 if some in-volume value of cells [z0, z1] x [y0, y1] x
+// [x0, x1] does not convert exactly under the item's maps (every thread of the
+// CTA calls it; the answer is the CTA's).  Thread t reads column x0 + t of
+// every row (coalesced), four rows' loads in flight at a time.
+static __device__ __noinline__ int item_exact_3d(const float* gx, const float* gy, long long pz, long long py, int z0,
+                                                 int z1, int y0, int y1, int x0, int x1, FxMap qx, FxMap qy) {
+  bool ok = true;
+  const int x = x0 + (int)threadIdx.x;
+  if (x <= x1) {
+    for (int z = z0; z <= z1; z++) {
+      for (int y = y0; y <= y1; y += 4) {
+        float a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const long long o = (long long)z * pz + (long long)min(y + u, y1) * py + x;
+          a[u] = gx[o];
+          b[u] = gy[o];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) ok = ok && fx_on_grid(a[u], qx) && fx_on_grid(b[u], qy);
+      }
+    }
+  }
+  return __syncthreads_or(!ok) ? 0 : 1;
+}
+
+// Recompute one lane's failing windows (bit 4a + c: output row a, column c of
+// the lane; centre plane zc, rows yc0 + a, columns xc0 + c) from their cells
+// and store them over the fixed-point results.
+struct Fix3D {
+  const float* gx;
+  const float* gy;
+  long long pz, py;
+  int Z, H, W, hz1, hz2, h1, h2, w1, w2, sz, sy, sx;
+  float* out;
+  long long opz, opy;
+};
+static __device__ __noinline__ void fixup_lane_3d(Fix3D f, uint32_t pending, int zc, int yc0, int xc0,
+                                                  uint32_t* status) {
+  for (; pending; pending &= pending - 1) {
+    const int bit = __ffs(pending) - 1;
+    const int yc = yc0 + (bit >> 2), xc = xc0 + (bit & 3);
+    FxBox b;
+    b.gx = f.gx;
+    b.gy = f.gy;
+    b.pz = f.pz;
+    b.py = f.py;
+    b.z0 = max(zc - f.hz1, 0);
+    b.z1 = min(zc + f.hz2, f.Z - 1);
+    b.y0 = max(yc - f.h1, 0);
+    b.y1 = min(yc + f.h2, f.H - 1);
+    b.x0 = max(xc - f.w1, 0);
+    b.x1 = min(xc + f.w2, f.W - 1);
+    f.out[(long long)(zc / f.sz) * f.opz + (long long)(yc / f.sy) * f.opy + xc / f.sx] = fx_recompute(b, status);
+  }
+}
+
+#ifndef SWC_K3D_MINB
+#define SWC_K3D_MINB 3  // resident CTAs per SM the 3-D kernel is compiled for
+#endif
 template <int TY, int TX, int KY, int KX>
-__global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constant__ K3DParams p) {
+__global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __grid_constant__ K3DParams p) {
   using G = Geo3D<TY, TX, KY, KX>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int esz = p.is_f32 ? 4 : 2;
@@ -89,6 +166,13 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
   uint64_t* bar = reinterpret_cast<uint64_t*>(VS + 8 * TY * G::VSP);      // 2 mbarriers (4 reserved)
   static_assert(G::TXI <= K3_THREADS, "one input column per thread");
   __shared__ float red[4][K3_THREADS / 32];
+  // item constants, uniform over the CTA, kept here rather than in registers:
+  // the float32 maps, the value G of an off-volume cell, the certificate's
+  // rounding bounds (0 once the item converts exactly; uint16 is exact)
+  __shared__ FxMap sh_qx, sh_qy;
+  __shared__ float sh_moff[2];
+  __shared__ int sh_G[2];
+  __shared__ float sh_rho[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
@@ -148,7 +232,6 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
     };
 
     // ---- float32: one fixed-point map for the item (pass over its planes)
-    float qmx = 0.f, qsx = 1.f, qmy = 0.f, qsy = 1.f;
     if (p.is_f32) {
       float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
       if (tid == 0 && p.use_tma) {
@@ -198,21 +281,24 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
         ylo = fminf(ylo, red[2][w]); yhi = fmaxf(yhi, red[3][w]);
       }
       __syncthreads();
-      auto mk = [&](float lo, float hi, float& m, float& s) {
-        if (!(lo <= hi)) lo = hi = 0.0f;
-        m = lo + 0.5f * (hi - lo);
-        const float A = fmaxf(hi - m, m - lo);
-        int e = 0;
-        if (A > 0.0f) {
-          int ea;
-          frexpf(A, &ea);
-          e = min(max(p.qbits - ea, -126), 126);
-        }
-        s = __int_as_float((127 + e) << 23);
-      };
-      mk(xlo, xhi, qmx, qsx);
-      mk(ylo, yhi, qmy, qsy);
+      if (tid == 0) {
+        const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
+        sh_qx = qx;
+        sh_qy = qy;
+        sh_moff[0] = (qx.C - kFxMagic) / qx.s;  // reference of off-volume planes (X = 0)
+        sh_moff[1] = (qy.C - kFxMagic) / qy.s;
+        sh_G[0] = fx_quant(0.0f, qx);
+        sh_G[1] = fx_quant(0.0f, qy);
+        sh_rho[0] = qx.rho;
+        sh_rho[1] = qy.rho;
+      }
+    } else if (tid == 0) {
+      sh_G[0] = sh_G[1] = 0;
+      sh_rho[0] = sh_rho[1] = 0.0f;
     }
+    // (the first step's barrier after the vertical pass orders these stores
+    // before their first reads in step 4)
+    int item_state = p.is_f32 ? -1 : 1;  // item converts exactly: -1 not yet known
 
     // ---- the z-march
     uint32_t V0[2][4], V1[2][4];
@@ -252,9 +338,17 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
         constexpr bool Y_IN = decltype(y_in_tag)::value;
         const int gxx = x0 - G::W1 + c;
         const bool col_ok = gxx >= 0 && gxx < p.W;
-        const float fse_x = (col_ok && ze_ok) ? qsx : 0.f, fsl_x = (col_ok && zl_ok) ? qsx : 0.f;
-        const float fse_y = (col_ok && ze_ok) ? qsy : 0.f, fsl_y = (col_ok && zl_ok) ? qsy : 0.f;
         const bool ue = col_ok && ze_ok, ul = col_ok && zl_ok;
+        // entering / leaving plane maps: off-volume planes convert to X = 0
+        FxMap qxe = sh_qx, qye = sh_qy, qxl = sh_qx, qyl = sh_qy;
+        if (!ze_ok) {
+          qxe.msub = sh_moff[0];
+          qye.msub = sh_moff[1];
+        }
+        if (!zl_ok) {
+          qxl.msub = sh_moff[0];
+          qyl.msub = sh_moff[1];
+        }
         uint32_t P0 = 0u, P1 = 0u;
         uint64_t P2 = 0ull, P3 = 0ull, P4 = 0ull;
         uint32_t S0[TY], S1[TY];
@@ -266,14 +360,14 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
           const int idx = r * G::BXW + G::COFF + c;
           int Xe, Xl, Ye, Yl;
           if (p.is_f32) {
+            // off-volume rows and columns are read as 0 and enter as G (step 4
+            // removes them); off-volume planes convert to 0
             const float* pe = reinterpret_cast<const float*>(se);
             const float* pl = reinterpret_cast<const float*>(sl);
-            const float xe = pe[idx], ye = pe[yoff + idx];
-            const float xl = has_leave ? pl[idx] : 0.f, yl = has_leave ? pl[yoff + idx] : 0.f;
-            Xe = __float_as_int(fmaf(xe - qmx, row_ok ? fse_x : 0.f, 12582912.0f)) - 0x4B400000;
-            Ye = __float_as_int(fmaf(ye - qmy, row_ok ? fse_y : 0.f, 12582912.0f)) - 0x4B400000;
-            Xl = __float_as_int(fmaf(xl - qmx, row_ok ? fsl_x : 0.f, 12582912.0f)) - 0x4B400000;
-            Yl = __float_as_int(fmaf(yl - qmy, row_ok ? fsl_y : 0.f, 12582912.0f)) - 0x4B400000;
+            Xe = fx_quant(pe[idx], qxe);
+            Ye = fx_quant(pe[yoff + idx], qye);
+            Xl = has_leave ? fx_quant(pl[idx], qxl) : 0;
+            Yl = has_leave ? fx_quant(pl[yoff + idx], qyl) : 0;
           } else {
             const uint16_t* pe = reinterpret_cast<const uint16_t*>(se);
             const uint16_t* pl = reinterpret_cast<const uint16_t*>(sl);
@@ -309,7 +403,6 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
             VS[7 * plane + base] = (uint32_t)(v4 >> 32);
           }
         }
-        (void)fsl_y;
       };
       const bool y_in = by >= 0 && by + G::TYI <= p.H;
       for (int c = tid; c < G::TXI; c += K3_THREADS) {
@@ -360,11 +453,44 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
         }
       }
 
-      // step 4 for the output plane whose window is complete
+      // step 4 for the output plane whose window is complete: Eq. 2 from the
+      // exact sums of window (a, c) with n in-volume cells; `fail` reports a
+      // float32 window whose certificate does not hold
+      const int Gx = sh_G[0], Gy = sh_G[1];
+      const float rhox = sh_rho[0], rhoy = sh_rho[1];
+      const bool Gchk = p.is_f32 != 0;
+      auto eval = [&](int a, int c, int cz, uint32_t n32, bool& fail) -> float {
+        uint32_t s0u = V0[a][c], s1u = V1[a][c];
+        uint64_t q2 = V2[a][c], q3 = V3[a][c], q4 = V4[a][c];
+        const int n_oob = cz * (KY * KX) - (int)n32;  // off-volume rows and columns of in-volume planes
+        if (n_oob != 0) {  // border: remove their constant contribution (G = 0 for uint16)
+          s0u -= (uint32_t)n_oob * (uint32_t)Gx;
+          s1u -= (uint32_t)n_oob * (uint32_t)Gy;
+          q2 -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gx);
+          q3 -= (uint64_t)n_oob * (uint64_t)((long long)Gy * Gy);
+          q4 -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gy);
+        }
+        // exact in 64-bit modular arithmetic; the results are below 2^63
+        const uint64_t n = n32;
+        const uint64_t nq2 = n * q2, nq3 = n * q3;
+        const uint64_t s0 = (uint64_t)(long long)(int)s0u, s1 = (uint64_t)(long long)(int)s1u;
+        const long long vx = (long long)(nq2 - s0 * s0);
+        const long long vy = (long long)(nq3 - s1 * s1);
+        const long long num = (long long)(n * q4 - s0 * s1);
+        const float rx = rsqrtf(i64_to_f32(vx)), ry = rsqrtf(i64_to_f32(vy));
+        const float z = (float)n32 * fmaf(rhox, fminf(rx, 3.0e38f), rhoy * fminf(ry, 3.0e38f));
+        // float32: the int32 reading of the first moments is exact while n Sxx < 2^62
+        fail = !(z <= 8.99e-6f) || (Gchk && ((nq2 | nq3) >> 62) != 0ull);
+        // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
+        return clamp1_nan(i64_to_f32(num) * rx * ry);
+      };
+      uint32_t pending = 0;  // bit 4a + c: window whose certificate failed
+      int zc_out = 0;
       if (!lane_on) {
       } else if (s >= p.kz - 1 && p.unit_stride) {
         // unit strides: output (z, y, x) = centre (z, y, x); 4 columns per lane
         const int zc = zc0 + (s - (p.kz - 1));
+        zc_out = zc;
         const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;
 #pragma unroll
         for (int a = 0; a < 2; a++) {
@@ -378,13 +504,9 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
           for (int c = 0; c < 4; c++) {
             const int xc = xc0 + c;
             const int cx = max(min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1, 0);
-            // n <= 32768 * 15: a 32-bit count keeps n * sum a 32 x 64-bit product
-            const uint64_t n = (uint32_t)(cz * cy * cx);
-            const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
-            const long long vx = (long long)(n * V2[a][c] - s0 * s0);
-            const long long vy = (long long)(n * V3[a][c] - s1 * s1);
-            const long long num = (long long)(n * V4[a][c] - s0 * s1);
-            res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
+            bool f;
+            res[c] = eval(a, c, cz, (uint32_t)(cz * cy * cx), f);
+            if (f && xc < p.W) pending |= 1u << (4 * a + c);
           }
           if (p.vec_store && xc0 + 3 < p.W) {
             stg128(orow + xc0, res[0], res[1], res[2], res[3]);
@@ -396,6 +518,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
         }
       } else if (s >= p.kz - 1) {
         const int zc = zc0 + (s - (p.kz - 1));
+        zc_out = zc;
         if (zc % p.sz == 0) {
           const int cz = min(zc + p.hz2, p.Z - 1) - max(zc - p.hz1, 0) + 1;
 #pragma unroll
@@ -409,18 +532,27 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k3d_kernel(const __grid_constan
               const int xc = x0 + 4 * lane + c;
               if (xc >= p.W || xc % p.sx != 0) continue;
               const int cx = min(xc + G::W2, p.W - 1) - max(xc - G::W1, 0) + 1;
-              const uint64_t n = (uint32_t)(cz * cy * cx);
-              const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
-              const long long vx = (long long)(n * V2[a][c] - s0 * s0);
-              const long long vy = (long long)(n * V3[a][c] - s1 * s1);
-              const long long num = (long long)(n * V4[a][c] - s0 * s1);
-              orow[xc / p.sx] =
-                  clamp1_nan(i64_to_f32(num) * rsqrtf(i64_to_f32(vx) * i64_to_f32(vy)));
+              bool f;
+              orow[xc / p.sx] = eval(a, c, cz, (uint32_t)(cz * cy * cx), f);
+              if (f) pending |= 1u << (4 * a + c);
             }
           }
         }
       }
-      __syncthreads();  // VS and the ring slots are reused next step
+      // VS and the ring slots are reused next step (this is the step's barrier)
+      if (__syncthreads_or(pending != 0)) {
+        if (item_state < 0) {
+          item_state = item_exact_3d((const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, max(ze0, 0),
+                                     min(ze0 + nsteps, p.Z) - 1, max(by, 0), min(by + G::TYI, p.H) - 1,
+                                     max(x0 - G::W1, 0), min(x0 - G::W1 + G::TXI, p.W) - 1, sh_qx, sh_qy);
+          if (item_state == 1 && tid == 0) sh_rho[0] = sh_rho[1] = 0.0f;  // read after the next step's barrier
+        }
+        if (item_state == 0 && pending) {
+          const Fix3D fx{(const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, p.Z, p.H, p.W, p.hz1, p.hz2,
+                         G::H1, G::H2, G::W1, G::W2, p.sz, p.sy, p.sx, p.out, p.opz, p.opy};
+          fixup_lane_3d(fx, pending, zc_out, y0 + warp * 2, x0 + 4 * lane, p.status);
+        }
+      }
     }
   }
 }

@@ -155,6 +155,18 @@ static int f32_qbits(uint64_t n) {
   return qb;
 }
 
+// Fixed-point bits of the 3-D float32 kernel, whose first-moment sums are
+// 64-bit: |X| < 2^q / 1.015625 + 1 (the map's margin and rounding), so
+// n (2^q / 1.015625 + 1) < 2^31.5 keeps n^2 var(X), the bound of
+// n Sxx - Sx^2 and of |n Sxy - Sx Sy|, below 2^63; the window sums of one
+// plane (ky kx cells) stay below 2^31; at most 22 bits.
+static int f32_qbits_3d(uint64_t n, uint64_t plane) {
+  int qb = 22;
+  auto mx = [&](int q) { return std::ldexp(1.0, q) / 1.015625 + 1.0; };
+  while (qb > 1 && ((double)n * mx(qb) >= 3.03e9 || (double)plane * mx(qb) >= 2147483648.0)) qb--;
+  return qb;
+}
+
 // Geometry, launch shape and per-launch constants of the 2-D kernels.
 swcorr_status setup_2d(const DeviceInfo& dev, swcorr_dtype dt, int H, int W, int kh, int kw, int sy, int sx,
                        Geo2DInfo* g2, K2DParams* k2, size_t* smem_out, int* grid_out, swcorr_tune* tune) {
@@ -410,6 +422,8 @@ static swcorr_status run_1d(swcorr_plan_s* p, const void* x, const void* y, floa
     k1.gx = x;
     k1.gy = y;
   }
+  k1.rx = x;
+  k1.ry = y;
   k1.out = c;
   k1.status = p->d_status;
   cudaError_t e = k1d_launch(k1, p->grid, p->warps, p->smem, st);
@@ -441,7 +455,7 @@ static swcorr_status plan_3d(swcorr_plan_s* p) {
   k3.nxb = (k3.W + g.TX - 1) / g.TX;
   k3.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
   const uint64_t n = (uint64_t)p->k[0] * p->k[1] * p->k[2];
-  k3.qbits = f32_qbits(n);
+  k3.qbits = f32_qbits_3d(n, (uint64_t)p->k[1] * p->k[2]);
   if (!k3.is_f32 && (uint64_t)std::min(k3.kz, k3.Z) * std::min(p->k[1], k3.H) * std::min(p->k[2], k3.W) > kMaxU16Cells)
     return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows are limited to %llu in-bounds cells",
                 (unsigned long long)kMaxU16Cells);
