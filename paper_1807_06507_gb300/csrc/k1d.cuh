@@ -124,11 +124,21 @@ static __device__ __noinline__ void lane_redo_1d(const float* sx_span, const flo
   const float* gy = sy_span - e0;
   const int ta = __ffsll((long long)fail) - 1, tb = 63 - __clzll((long long)fail);
   const long long a = max(0ll, (j_base + ta) * stride - h1), b = min(N - 1, (j_base + tb) * stride + h2);
-  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
-  for (long long i = a; i <= b; i++) {
-    const float u = gx[i], v = gy[i];
-    xlo = fminf(xlo, u); xhi = fmaxf(xhi, u); ylo = fminf(ylo, v); yhi = fmaxf(yhi, v);
+  // range of the span: four independent accumulators (the loop is latency-bound)
+  float rlo[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f}, rhi[4] = {-3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
+  float slo[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f}, shi[4] = {-3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
+  for (long long i = a; i <= b; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const long long iu = min(i + u, b);
+      const float p = gx[iu], v = gy[iu];
+      rlo[u] = fminf(rlo[u], p); rhi[u] = fmaxf(rhi[u], p); slo[u] = fminf(slo[u], v); shi[u] = fmaxf(shi[u], v);
+    }
   }
+  const float xlo = fminf(fminf(rlo[0], rlo[1]), fminf(rlo[2], rlo[3]));
+  const float xhi = fmaxf(fmaxf(rhi[0], rhi[1]), fmaxf(rhi[2], rhi[3]));
+  const float ylo = fminf(fminf(slo[0], slo[1]), fminf(slo[2], slo[3]));
+  const float yhi = fmaxf(fmaxf(shi[0], shi[1]), fmaxf(shi[2], shi[3]));
   if (xlo == xhi || ylo == yhi) {  // a channel whose span is one value: every window is constant
     uint32_t count = 0;
     for (int t = ta; t <= tb; t++)
@@ -153,9 +163,25 @@ static __device__ __noinline__ void lane_redo_1d(const float* sx_span, const flo
     const long long j = j_base + t;
     if (j >= n_out) break;
     const long long nlo = max(0ll, j * stride - h1), nhi = min(N - 1, j * stride + h2);
-    if (nlo > hi) {  // no overlap with the previous window: start again
-      Sx = Sy = Sxx = Syy = Sxy = 0;
-      for (long long i = nlo; i <= nhi; i++) cell(i, 1);
+    if (nlo > hi) {  // no overlap with the previous window: start again, four partial sums at a time
+      long long p[4][5] = {};
+      bool okx = true, oky = true;
+      long long i = nlo;
+      for (; i + 3 <= nhi; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const long long X = fx_wide_quant(gx[i + u], wx, okx), Y = fx_wide_quant(gy[i + u], wy, oky);
+          p[u][0] += X; p[u][1] += Y; p[u][2] += X * X; p[u][3] += Y * Y; p[u][4] += X * Y;
+        }
+      }
+      gx_ok = gx_ok && okx;
+      gy_ok = gy_ok && oky;
+      Sx = p[0][0] + p[1][0] + p[2][0] + p[3][0];
+      Sy = p[0][1] + p[1][1] + p[2][1] + p[3][1];
+      Sxx = p[0][2] + p[1][2] + p[2][2] + p[3][2];
+      Syy = p[0][3] + p[1][3] + p[2][3] + p[3][3];
+      Sxy = p[0][4] + p[1][4] + p[2][4] + p[3][4];
+      for (; i <= nhi; i++) cell(i, 1);
     } else {
       for (long long i = lo; i < nlo; i++) cell(i, -1);
       for (long long i = hi + 1; i <= nhi; i++) cell(i, 1);

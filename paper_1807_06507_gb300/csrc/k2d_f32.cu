@@ -6,10 +6,10 @@
 
 namespace swc {
 
-template <int M, int KW, bool TMA>
 #ifndef SWC_K2DF_MINB
 #define SWC_K2DF_MINB 12  // resident one-warp CTAs per SM the float32 2-D kernel is compiled for
 #endif
+template <int M, int KW, bool TMA>
 __global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
   using G = Geo2DF<M, KW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -21,6 +21,10 @@ __global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid
   rg.lx = rg.ry + (size_t)p.NR * G::RWS;
   rg.ly = rg.lx + (size_t)p.NR * G::RWS;
   rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
+  __shared__ uint64_t pend[kPend2D];  // windows whose quick certificate test failed
+  __shared__ int npend;
+  rg.pend = pend;
+  rg.npend = &npend;
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
     fence_mbar_init();

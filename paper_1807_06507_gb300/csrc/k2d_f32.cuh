@@ -31,11 +31,12 @@
 //    rounds once to float32 per factor.  A zero variance gives NaN exactly.
 //  * Each window's result is certified (fxmap.cuh): with rho the lane's
 //    rounding bound, |dc| <= rho n (1/sqrt(vx) + 1/sqrt(vy)) + 7e-7.  The
-//    common case passes a one-comparison-per-channel test.  When a window of
-//    some lane does not, the whole warp determines, once per item, which of
-//    its lanes convert exactly (rho = 0, every window certified); a failing
-//    window of an inexact lane is recomputed from its own cells and stored
-//    over the fixed-point result.
+//    common case passes a one-comparison-per-channel test (lanes of integer
+//    data on a grid step of at most 1 convert exactly, rho = 0: nothing to
+//    test).  A window that does not pass is listed; after the item, each lane
+//    with listed windows determines whether its values convert exactly, and
+//    the listed windows of the other lanes are recomputed from their own
+//    cells and stored over the fixed-point results.
 #pragma once
 
 #include <type_traits>
@@ -72,7 +73,11 @@ struct Ring2DF {
   uint64_t* bar;  // [NR]
   int NR;
   int PF;
+  uint64_t* pend; // windows whose quick certificate test failed: row << 8 | lane << 3 | column
+  int* npend;     //   (at most kPend2D per item; the count may run past it)
 };
+
+constexpr int kPend2D = 256;
 
 // Fix-up of one output row of a lane: every window flagged in `fail`
 // (bit c: centre column cl + c) is recomputed from its own cells
@@ -81,7 +86,7 @@ struct FixScene2D {  // the fields of a scene the fix-up reads (passed by value)
   const float* gx;
   const float* gy;
   long long in_pitch;
-  int H, W, h1, h2, kw, sx;
+  int H, W, h1, h2, kw, sx, sy;
 };
 
 // Whether every in-grid value of a lane's item (rows [r0, r1), the lane's
@@ -116,24 +121,49 @@ static __device__ __noinline__ bool lane_exact_2d(const float* gx, const float* 
   return false;
 }
 
-static __device__ __noinline__ void fixup_row_2d(FixScene2D sc, uint32_t fail, int rc, int cl, float* orow,
-                                                 uint32_t* status) {
-  const int w1 = (sc.kw - 1) / 2, w2 = sc.kw / 2;
-  for (; fail; fail &= fail - 1) {
-    const int cc = cl + (__ffs(fail) - 1);
-    if (cc >= sc.W || (sc.sx != 1 && cc % sc.sx != 0)) continue;
-    FxBox b;
-    b.gx = sc.gx;
-    b.gy = sc.gy;
-    b.pz = 0;
-    b.py = sc.in_pitch;
-    b.z0 = b.z1 = 0;
-    b.y0 = max(rc - sc.h1, 0);
-    b.y1 = min(rc + sc.h2, sc.H - 1);
-    b.x0 = max(cc - w1, 0);
-    b.x1 = min(cc + w2, sc.W - 1);
-    orow[sc.sx == 1 ? cc : cc / sc.sx] = fx_recompute(b, status);
+// Recompute the window of centre (rc, cc) from its cells (fx_recompute) and
+// store it over the fixed-point result.
+static __device__ __noinline__ void fixup_window_2d(const FixScene2D& sc, float* out, long long out_pitch, int jr,
+                                                    int cc, uint32_t* status) {
+  if (cc >= sc.W || (sc.sx != 1 && cc % sc.sx != 0)) return;
+  const int rc = jr * sc.sy, w1 = (sc.kw - 1) / 2, w2 = sc.kw / 2;
+  FxBox b;
+  b.gx = sc.gx;
+  b.gy = sc.gy;
+  b.pz = 0;
+  b.py = sc.in_pitch;
+  b.z0 = b.z1 = 0;
+  b.y0 = max(rc - sc.h1, 0);
+  b.y1 = min(rc + sc.h2, sc.H - 1);
+  b.x0 = max(cc - w1, 0);
+  b.x1 = min(cc + w2, sc.W - 1);
+  out[(long long)jr * out_pitch + (sc.sx == 1 ? cc : cc / sc.sx)] = fx_recompute(b, status);
+}
+
+// The failing windows of a work item, after its row march (the whole warp
+// calls it): each lane with a listed window (or an overflow) learns whether
+// its values convert exactly; the listed windows of the other lanes are
+// recomputed by the warp in parallel, and a lane that overflowed the list
+// recomputes all its windows (output rows [j0, j1), columns cl + 0..M-1).
+template <int M, int NCOL>
+static __device__ __noinline__ void fixup_item_2d(FixScene2D sc, float* out, long long out_pitch, const uint64_t* pend,
+                                                  int n, bool need, bool ovf, int exact_state, int r0, int r1, int cl,
+                                                  int w1, int j0, int j1, FxMap qx, FxMap qy, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  if (need && exact_state < 0)
+    exact_state = lane_exact_2d<NCOL>(sc.gx, sc.gy, sc.in_pitch, r0, r1, cl - w1, max(0, w1 - cl),
+                                      min(NCOL, sc.W - (cl - w1)), qx, qy)
+                      ? 1
+                      : 0;
+  const uint32_t inexact = __ballot_sync(0xffffffffu, need && exact_state == 0);
+  for (int i = lane; i < min(n, kPend2D); i += 32) {
+    const uint64_t e = pend[i];
+    const int l = (int)(e >> 3) & 31;
+    if ((inexact >> l) & 1u) fixup_window_2d(sc, out, out_pitch, (int)(e >> 8), cl - M * lane + M * l + (int)(e & 7), status);
   }
+  if (ovf && exact_state == 0)
+    for (int jr = j0; jr < j1; jr++)
+      for (int c = 0; c < M; c++) fixup_window_2d(sc, out, out_pitch, jr, cl + c, status);
 }
 
 template <int M, int KW, bool TMA>
@@ -239,6 +269,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
 
   // ---- pass 1: value range of the lane's columns over the item's rows
   float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+  bool allint = true;  // every value an integer (then, with s >= 1, every value converts exactly)
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
   if (!stream_rows(false, [&](int i, uint32_t s, auto) {
@@ -258,6 +289,10 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
               xhi = fmaxf(xhi, va[u]);
               ylo = fminf(ylo, vb[u]);
               yhi = fmaxf(yhi, vb[u]);
+              // |v| + 1.5*2^23 rounds |v| < 2^22 to an integer (larger |v| may
+              // fail the test; they are then checked in full if needed)
+              allint = allint && (fabsf(va[u]) + kFxMagic) - kFxMagic == fabsf(va[u]) &&
+                       (fabsf(vb[u]) + kFxMagic) - kFxMagic == fabsf(vb[u]);
             }
           }
         }
@@ -272,13 +307,18 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   const int Gx = fx_quant(0.0f, qx), Gy = fx_quant(0.0f, qy);  // value of an off-grid column
   // quick certificate: vx >= (rho n / 4.5e-6)^2 with n the interior count
   // (border windows have fewer cells, so the test is conservative there)
-  int exact_state = -1;  // lane exactness: -1 not yet known, 0 no, 1 yes
-  float Kx, Ky;
+  // lane exactness: -1 not yet known, 0 no, 1 yes (integers on a grid step of
+  // at most 1: x - m and (x - m) s are exact)
+  const int exact_state = (allint && qx.s >= 1.0f && qy.s >= 1.0f) ? 1 : -1;
+  bool need = false, ovf = false;  // the lane listed failing windows; its list overflowed
+  if (lane == 0) *rg.npend = 0;
+  __syncwarp();
+  float Kx, Ky;  // quick certificate thresholds, fixed for the item
   {
     const float nmax = (float)(sc.kh * KW);
     const float k0 = 4.9432e10f * nmax * nmax;  // (1 / 4.5e-6)^2 * 1.001
-    Kx = k0 * qx.rho * qx.rho;
-    Ky = k0 * qy.rho * qy.rho;
+    Kx = exact_state == 1 ? 0.0f : k0 * qx.rho * qx.rho;
+    Ky = exact_state == 1 ? 0.0f : k0 * qy.rho * qy.rho;
   }
 
   const bool fast_cols = sc.sx == 1 && sc.vec_store;
@@ -386,7 +426,9 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
         const float fvx = i64_to_f32(vx), fvy = i64_to_f32(vy);
         // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
         res[c] = clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
-        fail |= (fvx >= Kx && fvy >= Ky) ? 0u : (1u << c);
+        // windows past the grid's last column have no certificate to pass
+        // (strided plans drop non-output columns in the fix-up)
+        fail |= (fvx >= Kx && fvy >= Ky) || cl + c >= sc.W ? 0u : (1u << c);
       }
       if (fast_cols && cl + M <= sc.W) {
 #pragma unroll
@@ -398,20 +440,17 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
           if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) orow[sc.sx == 1 ? cc : cc / sc.sx] = res[c];
         }
       }
-      // certificate: once per item, when a lane of the warp has a failing
-      // window, every lane learns whether its values convert exactly
-      if (__any_sync(0xffffffffu, fail != 0u && exact_state < 0)) {
-        if (exact_state < 0) {
-          const bool ok = lane_exact_2d<G::NCOL>((const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, max(t0, 0),
-                                                 min(t0 + nrows, sc.H), cl - G::W1, max(0, G::W1 - cl),
-                                                 min(G::NCOL, sc.W - (cl - G::W1)), qx, qy);
-          exact_state = ok ? 1 : 0;
-          if (ok) Kx = Ky = 0.0f;
+      // rare: list the failing windows (recomputed after the item, unless the
+      // lane converts exactly)
+      if (fail != 0u && exact_state != 1) {
+        for (uint32_t f = fail; f; f &= f - 1) {
+          const int k = atomicAdd(rg.npend, 1);
+          if (k < kPend2D)
+            rg.pend[k] = ((uint64_t)jr << 8) | ((uint64_t)lane << 3) | (uint64_t)(__ffs(f) - 1);
+          else
+            ovf = true;
         }
-      }
-      if (fail != 0u && exact_state == 0) {
-        const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, KW, sc.sx};
-        fixup_row_2d(fs, fail, rc, cl, orow, status);
+        need = true;
       }
       if (lane_border) {
         // restore the running sums for the next rows
@@ -430,7 +469,15 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
     until_out--;
   });
   (void)seq0;
-  return ok;
+  if (!ok) return false;
+  __syncwarp();
+  if (__any_sync(0xffffffffu, need)) {
+    const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, KW, sc.sx,
+                        sc.sy};
+    fixup_item_2d<M, G::NCOL>(fs, sc.out, sc.out_pitch, rg.pend, *rg.npend, need, ovf, exact_state, max(t0, 0),
+                              min(t0 + nrows, sc.H), cl, G::W1, j0, j1, qx, qy, status);
+  }
+  return true;
 }
 
 }  // namespace swc

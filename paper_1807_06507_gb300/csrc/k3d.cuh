@@ -17,12 +17,9 @@
 //    map's 1/64 margin) and a plane's window sums fit in int32.  The window's
 //    sum of X is kept modulo 2^32: it is exact as an int32 whenever
 //    n Sxx < 2^62 (Cauchy-Schwarz: |Sx| <= sqrt(n Sxx) < 2^31); a window
-//    beyond that is treated as one whose certificate fails.  Planes
-//    outside the volume switch the map's reference to m' = (C - 1.5*2^23)/s,
-//    which converts their zero fill to X = 0; off-volume rows and columns of
-//    a plane (read as 0, off-volume in the entering and the leaving plane
-//    alike) enter as the constant G = X(0), and step 4 of a border window
-//    subtracts their count times G, G^2 and Gx*Gy exactly.
+//    beyond that is treated as one whose certificate fails.  Off-volume cells
+//    convert to X = 0 through a zero scale and the plain rounding constant
+//    1.5*2^23, switched per plane, column and row.
 //  * Vertical pass: one thread per input column forms, for every row of the
 //    rectangle, the five entering-minus-leaving streams (x, y, x^2, y^2, xy
 //    differences), their running prefix down the column, and the window sums
@@ -116,9 +113,7 @@ static __device__ __noinline__ int item_exact_3d(const float* gx, const float* g
   return __syncthreads_or(!ok) ? 0 : 1;
 }
 
-// Recompute one lane's failing windows (bit 4a + c: output row a, column c of
-// the lane; centre plane zc, rows yc0 + a, columns xc0 + c) from their cells
-// and store them over the fixed-point results.
+// Geometry a fix-up needs (passed by value).
 struct Fix3D {
   const float* gx;
   const float* gy;
@@ -127,23 +122,46 @@ struct Fix3D {
   float* out;
   long long opz, opy;
 };
-static __device__ __noinline__ void fixup_lane_3d(Fix3D f, uint32_t pending, int zc, int yc0, int xc0,
-                                                  uint32_t* status) {
-  for (; pending; pending &= pending - 1) {
-    const int bit = __ffs(pending) - 1;
-    const int yc = yc0 + (bit >> 2), xc = xc0 + (bit & 3);
-    FxBox b;
-    b.gx = f.gx;
-    b.gy = f.gy;
-    b.pz = f.pz;
-    b.py = f.py;
-    b.z0 = max(zc - f.hz1, 0);
-    b.z1 = min(zc + f.hz2, f.Z - 1);
-    b.y0 = max(yc - f.h1, 0);
-    b.y1 = min(yc + f.h2, f.H - 1);
-    b.x0 = max(xc - f.w1, 0);
-    b.x1 = min(xc + f.w2, f.W - 1);
-    f.out[(long long)(zc / f.sz) * f.opz + (long long)(yc / f.sy) * f.opy + xc / f.sx] = fx_recompute(b, status);
+
+// Recompute the window of centre (zc, yc, xc) from its cells (fx_recompute)
+// and store it over the fixed-point result.
+static __device__ __noinline__ void fixup_window_3d(const Fix3D& f, int zc, int yc, int xc, uint32_t* status) {
+  FxBox b;
+  b.gx = f.gx;
+  b.gy = f.gy;
+  b.pz = f.pz;
+  b.py = f.py;
+  b.z0 = max(zc - f.hz1, 0);
+  b.z1 = min(zc + f.hz2, f.Z - 1);
+  b.y0 = max(yc - f.h1, 0);
+  b.y1 = min(yc + f.h2, f.H - 1);
+  b.x0 = max(xc - f.w1, 0);
+  b.x1 = min(xc + f.w2, f.W - 1);
+  f.out[(long long)(zc / f.sz) * f.opz + (long long)(yc / f.sy) * f.opy + xc / f.sx] = fx_recompute(b, status);
+}
+
+// The item's failing windows, after its z-march: the CTA learns whether the
+// item's values convert exactly (then every result stands); otherwise each
+// listed window (n <= cap entries: centre plane << 10 | thread << 3 | bit
+// 4a + c) is recomputed, or, if the list overflowed, every output window of
+// the item (planes [zc0, zc1), rows [y0, y0 + ty), columns [x0, x0 + tx)).
+static __device__ __noinline__ void fixup_item_3d(Fix3D f, const uint64_t* list, int n, int cap, int y0, int x0,
+                                                  int zc0, int zc1, int ty, int tx, int z0, int z1, int ry0,
+                                                  int ry1, int rx0, int rx1, FxMap qx, FxMap qy, uint32_t* status) {
+  if (item_exact_3d(f.gx, f.gy, f.pz, f.py, z0, z1, ry0, ry1, rx0, rx1, qx, qy)) return;
+  if (n <= cap) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t e = list[i];
+      const int zc = (int)(e >> 10), t = (int)(e >> 3) & 127, bit = (int)(e & 7);
+      fixup_window_3d(f, zc, y0 + (t >> 5) * 2 + (bit >> 2), x0 + 4 * (t & 31) + (bit & 3), status);
+    }
+    return;
+  }
+  const long long total = (long long)(zc1 - zc0) * ty * tx;
+  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+    const int xc = x0 + (int)(i % tx), yc = y0 + (int)((i / tx) % ty), zc = zc0 + (int)(i / ((long long)tx * ty));
+    if (xc < f.W && yc < f.H && zc % f.sz == 0 && yc % f.sy == 0 && xc % f.sx == 0)
+      fixup_window_3d(f, zc, yc, xc, status);
   }
 }
 
@@ -170,9 +188,11 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
   // the float32 maps, the value G of an off-volume cell, the certificate's
   // rounding bounds (0 once the item converts exactly; uint16 is exact)
   __shared__ FxMap sh_qx, sh_qy;
-  __shared__ float sh_moff[2];
-  __shared__ int sh_G[2];
   __shared__ float sh_rho[2];
+  // windows whose certificate failed during the item's z-march
+  constexpr int kPendCap = 384;
+  __shared__ uint64_t sh_pend[kPendCap];
+  __shared__ int sh_npend;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
@@ -231,6 +251,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       }
     };
 
+    if (tid == 0) sh_npend = 0;  // (ordered by the barriers of the range pass or the first step)
     // ---- float32: one fixed-point map for the item (pass over its planes)
     if (p.is_f32) {
       float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
@@ -285,20 +306,14 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
         const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
         sh_qx = qx;
         sh_qy = qy;
-        sh_moff[0] = (qx.C - kFxMagic) / qx.s;  // reference of off-volume planes (X = 0)
-        sh_moff[1] = (qy.C - kFxMagic) / qy.s;
-        sh_G[0] = fx_quant(0.0f, qx);
-        sh_G[1] = fx_quant(0.0f, qy);
         sh_rho[0] = qx.rho;
         sh_rho[1] = qy.rho;
       }
     } else if (tid == 0) {
-      sh_G[0] = sh_G[1] = 0;
       sh_rho[0] = sh_rho[1] = 0.0f;
     }
     // (the first step's barrier after the vertical pass orders these stores
     // before their first reads in step 4)
-    int item_state = p.is_f32 ? -1 : 1;  // item converts exactly: -1 not yet known
 
     // ---- the z-march
     uint32_t V0[2][4], V1[2][4];
@@ -339,16 +354,13 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
         const int gxx = x0 - G::W1 + c;
         const bool col_ok = gxx >= 0 && gxx < p.W;
         const bool ue = col_ok && ze_ok, ul = col_ok && zl_ok;
-        // entering / leaving plane maps: off-volume planes convert to X = 0
-        FxMap qxe = sh_qx, qye = sh_qy, qxl = sh_qx, qyl = sh_qy;
-        if (!ze_ok) {
-          qxe.msub = sh_moff[0];
-          qye.msub = sh_moff[1];
-        }
-        if (!zl_ok) {
-          qxl.msub = sh_moff[0];
-          qyl.msub = sh_moff[1];
-        }
+        // float32: a zero scale and the plain rounding constant convert
+        // off-volume cells to X = 0
+        const float mx = sh_qx.msub, my = sh_qy.msub;
+        const float fse_x = ue ? sh_qx.s : 0.f, fsl_x = ul ? sh_qx.s : 0.f;
+        const float fse_y = ue ? sh_qy.s : 0.f, fsl_y = ul ? sh_qy.s : 0.f;
+        const float fce_x = ue ? sh_qx.C : kFxMagic, fcl_x = ul ? sh_qx.C : kFxMagic;
+        const float fce_y = ue ? sh_qy.C : kFxMagic, fcl_y = ul ? sh_qy.C : kFxMagic;
         uint32_t P0 = 0u, P1 = 0u;
         uint64_t P2 = 0ull, P3 = 0ull, P4 = 0ull;
         uint32_t S0[TY], S1[TY];
@@ -360,14 +372,16 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
           const int idx = r * G::BXW + G::COFF + c;
           int Xe, Xl, Ye, Yl;
           if (p.is_f32) {
-            // off-volume rows and columns are read as 0 and enter as G (step 4
-            // removes them); off-volume planes convert to 0
             const float* pe = reinterpret_cast<const float*>(se);
             const float* pl = reinterpret_cast<const float*>(sl);
-            Xe = fx_quant(pe[idx], qxe);
-            Ye = fx_quant(pe[yoff + idx], qye);
-            Xl = has_leave ? fx_quant(pl[idx], qxl) : 0;
-            Yl = has_leave ? fx_quant(pl[yoff + idx], qyl) : 0;
+            const float xl = has_leave ? pl[idx] : 0.f, yl = has_leave ? pl[yoff + idx] : 0.f;
+            auto cv = [&](float v, float m, float sc, float cc) {
+              return __float_as_int(fmaf(v - m, row_ok ? sc : 0.f, row_ok ? cc : kFxMagic)) - 0x4B400000;
+            };
+            Xe = cv(pe[idx], mx, fse_x, fce_x);
+            Ye = cv(pe[yoff + idx], my, fse_y, fce_y);
+            Xl = cv(xl, mx, fsl_x, fcl_x);
+            Yl = cv(yl, my, fsl_y, fcl_y);
           } else {
             const uint16_t* pe = reinterpret_cast<const uint16_t*>(se);
             const uint16_t* pl = reinterpret_cast<const uint16_t*>(sl);
@@ -456,33 +470,31 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       // step 4 for the output plane whose window is complete: Eq. 2 from the
       // exact sums of window (a, c) with n in-volume cells; `fail` reports a
       // float32 window whose certificate does not hold
-      const int Gx = sh_G[0], Gy = sh_G[1];
       const float rhox = sh_rho[0], rhoy = sh_rho[1];
-      const bool Gchk = p.is_f32 != 0;
+      // quick certificate thresholds (rho n / 4.5e-6)^2 for the full window
+      const float k0 = 4.9432e10f * (float)(p.kz * KY * KX) * (float)(p.kz * KY * KX);
+      const float Kx = k0 * rhox * rhox, Ky = k0 * rhoy * rhoy;
+      const bool f32 = p.is_f32 != 0;
       auto eval = [&](int a, int c, int cz, uint32_t n32, bool& fail) -> float {
-        uint32_t s0u = V0[a][c], s1u = V1[a][c];
-        uint64_t q2 = V2[a][c], q3 = V3[a][c], q4 = V4[a][c];
-        const int n_oob = cz * (KY * KX) - (int)n32;  // off-volume rows and columns of in-volume planes
-        if (n_oob != 0) {  // border: remove their constant contribution (G = 0 for uint16)
-          s0u -= (uint32_t)n_oob * (uint32_t)Gx;
-          s1u -= (uint32_t)n_oob * (uint32_t)Gy;
-          q2 -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gx);
-          q3 -= (uint64_t)n_oob * (uint64_t)((long long)Gy * Gy);
-          q4 -= (uint64_t)n_oob * (uint64_t)((long long)Gx * Gy);
-        }
         // exact in 64-bit modular arithmetic; the results are below 2^63
         const uint64_t n = n32;
-        const uint64_t nq2 = n * q2, nq3 = n * q3;
-        const uint64_t s0 = (uint64_t)(long long)(int)s0u, s1 = (uint64_t)(long long)(int)s1u;
+        const uint64_t nq2 = n * V2[a][c], nq3 = n * V3[a][c];
+        const uint64_t s0 = (uint64_t)(long long)(int)V0[a][c], s1 = (uint64_t)(long long)(int)V1[a][c];
         const long long vx = (long long)(nq2 - s0 * s0);
         const long long vy = (long long)(nq3 - s1 * s1);
-        const long long num = (long long)(n * q4 - s0 * s1);
-        const float rx = rsqrtf(i64_to_f32(vx)), ry = rsqrtf(i64_to_f32(vy));
-        const float z = (float)n32 * fmaf(rhox, fminf(rx, 3.0e38f), rhoy * fminf(ry, 3.0e38f));
-        // float32: the int32 reading of the first moments is exact while n Sxx < 2^62
-        fail = !(z <= 8.99e-6f) || (Gchk && ((nq2 | nq3) >> 62) != 0ull);
+        const long long num = (long long)(n * V4[a][c] - s0 * s1);
+        const float fvx = i64_to_f32(vx), fvy = i64_to_f32(vy);
+        // float32 certificate: the quick per-channel test, the precise sum
+        // when it fails; the first moments read as int32 are exact while
+        // n Sxx < 2^62 (a window beyond that fails)
+        fail = false;
+        if (f32) {
+          const bool wide = ((nq2 | nq3) >> 62) != 0ull;
+          fail = wide || !(fvx >= Kx && fvy >= Ky);
+          if (fail && !wide) fail = !((float)n32 * (rhox * rsqrtf(fvx) + rhoy * rsqrtf(fvy)) <= 8.99e-6f);
+        }
         // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
-        return clamp1_nan(i64_to_f32(num) * rx * ry);
+        return clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
       };
       uint32_t pending = 0;  // bit 4a + c: window whose certificate failed
       int zc_out = 0;
@@ -540,19 +552,20 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
         }
       }
       // VS and the ring slots are reused next step (this is the step's barrier)
-      if (__syncthreads_or(pending != 0)) {
-        if (item_state < 0) {
-          item_state = item_exact_3d((const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, max(ze0, 0),
-                                     min(ze0 + nsteps, p.Z) - 1, max(by, 0), min(by + G::TYI, p.H) - 1,
-                                     max(x0 - G::W1, 0), min(x0 - G::W1 + G::TXI, p.W) - 1, sh_qx, sh_qy);
-          if (item_state == 1 && tid == 0) sh_rho[0] = sh_rho[1] = 0.0f;  // read after the next step's barrier
-        }
-        if (item_state == 0 && pending) {
-          const Fix3D fx{(const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, p.Z, p.H, p.W, p.hz1, p.hz2,
-                         G::H1, G::H2, G::W1, G::W2, p.sz, p.sy, p.sx, p.out, p.opz, p.opy};
-          fixup_lane_3d(fx, pending, zc_out, y0 + warp * 2, x0 + 4 * lane, p.status);
-        }
+      for (; pending; pending &= pending - 1) {  // rare: list the failing windows
+        const int k = atomicAdd(&sh_npend, 1);
+        if (k < kPendCap) sh_pend[k] = ((uint64_t)zc_out << 10) | ((uint64_t)tid << 3) | (uint64_t)(__ffs(pending) - 1);
       }
+      __syncthreads();  // VS and the ring slots are reused next step
+    }
+    // the item's failing windows (float32 only), once its z-march is done
+    if (p.is_f32 && sh_npend > 0) {
+      const Fix3D fx{(const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, p.Z, p.H, p.W, p.hz1, p.hz2,
+                     G::H1, G::H2, G::W1, G::W2, p.sz, p.sy, p.sx, p.out, p.opz, p.opy};
+      fixup_item_3d(fx, sh_pend, sh_npend, kPendCap, y0, x0, zc0, zc1, TY, TX, max(ze0, 0),
+                    min(ze0 + nsteps, p.Z) - 1, max(by, 0), min(by + G::TYI, p.H) - 1, max(x0 - G::W1, 0),
+                    min(x0 - G::W1 + G::TXI, p.W) - 1, sh_qx, sh_qy, p.status);
+      __syncthreads();  // the list and the item constants are reset by the next item
     }
   }
 }
