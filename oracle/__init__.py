@@ -53,6 +53,10 @@ def _configure(lib):
                              ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
                              dp, dp, dp, ctypes.c_int]
     lib.swo_corr.restype = ctypes.c_int
+    lib.swo_corr_border.argtypes = [ctypes.c_int, i64p, i32p, i32p, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
+                                    dp, dp, dp, ctypes.c_int, ctypes.c_int]
+    lib.swo_corr_border.restype = ctypes.c_int
     lib.swo_sums_u16.argtypes = [ctypes.c_int, i64p, i32p, i32p,
                                  ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_int64,
                                  i64p, ctypes.c_int]
@@ -111,7 +115,10 @@ def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
-def corr(x, y, k, stride=None, idx=None, threads=None, relvar=False):
+BORDERS = {"clip": 0, "paper": 1}
+
+
+def corr(x, y, k, stride=None, idx=None, threads=None, relvar=False, border="clip"):
     """Pearson c per output window (float64), NaN for constant windows.
 
     x, y: same-shape uint16 or float32 arrays (1 to 8 dims, C order).
@@ -120,8 +127,12 @@ def corr(x, y, k, stride=None, idx=None, threads=None, relvar=False):
     given, the result is 1-D with one entry per index.  Otherwise it has the
     output grid's shape, ceil(N_d / stride_d) per dimension.
     relvar=True also returns (relvar_x, relvar_y).
+    border: "clip" (windows clipped to the grid, n = in-grid cells) or
+    "paper" (Section 3's convention: -2 for a window past an edge or holding
+    a value <= -999 in x or y; the relative variances are 0 there).
     """
     x, y, dt, shape, k, stride, oshape = _args(x, y, k, stride)
+    bmode = BORDERS[border]
     if idx is not None:
         idx = np.ascontiguousarray(idx, dtype=np.int64).ravel()
         n = idx.size
@@ -130,11 +141,11 @@ def corr(x, y, k, stride=None, idx=None, threads=None, relvar=False):
     c = np.empty(n, dtype=np.float64)
     rx = np.empty(n, dtype=np.float64) if relvar else None
     ry = np.empty(n, dtype=np.float64) if relvar else None
-    rc = _load().swo_corr(x.ndim, _ptr(shape, ctypes.c_int64), _ptr(k, ctypes.c_int32),
-                          _ptr(stride, ctypes.c_int32), dt, x.ctypes.data, y.ctypes.data,
-                          _ptr(idx, ctypes.c_int64), n, _ptr(c, ctypes.c_double),
-                          _ptr(rx, ctypes.c_double), _ptr(ry, ctypes.c_double),
-                          int(threads or default_threads()))
+    rc = _load().swo_corr_border(x.ndim, _ptr(shape, ctypes.c_int64), _ptr(k, ctypes.c_int32),
+                                 _ptr(stride, ctypes.c_int32), dt, x.ctypes.data, y.ctypes.data,
+                                 _ptr(idx, ctypes.c_int64), n, _ptr(c, ctypes.c_double),
+                                 _ptr(rx, ctypes.c_double), _ptr(ry, ctypes.c_double), bmode,
+                                 int(threads or default_threads()))
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
     if idx is None:

@@ -21,6 +21,11 @@
  *   - relvar_x = sxx / sum(x^2) (and likewise for y): the fraction of the
  *     second moment that is variance; it says how much cancellation a
  *     sums-form evaluation (Eq. 2) of that window suffers.
+ * Border rule (border = 1, the paper's result convention, Section 3: the
+ * paragraph on the result set): a window that reaches past an edge of the
+ * grid in any dimension gives -2, and so does a window holding a missing
+ * value (a value <= -999) in x or in y; the other windows follow the rules
+ * above (they are never clipped).  border = 0 clips as above.
  * For uint16 data it also gives the five exact integer window sums
  * (sum x, sum y, sum x^2, sum y^2, sum xy) that the optimized algorithm's
  * steps 1-3 (Section 1) produce, by brute force over the window.
@@ -53,6 +58,7 @@ typedef struct {
   int64_t n_out;
   double *c, *rvx, *rvy; /* each may be NULL */
   int64_t *sums;         /* n_out x 5, uint16 only; may be NULL */
+  int border;            /* 0: clipped windows; 1: the paper's -2 convention */
   int64_t begin, end;
 } swo_job;
 
@@ -61,20 +67,24 @@ static double value_at(int dtype, const void *p, int64_t off) {
   return (double)((const float *)p)[off];
 }
 
-/* Window bounds [lo_d, hi_d] of output flat index o. */
-static void window_of(const swo_job *J, int64_t o, int64_t *lo, int64_t *hi) {
+/* Window bounds [lo_d, hi_d] of output flat index o, clipped to the grid;
+ * returns 1 if the unclipped window reaches past an edge in some dimension. */
+static int window_of(const swo_job *J, int64_t o, int64_t *lo, int64_t *hi) {
   int64_t j[SWO_MAXDIM];
   for (int d = J->ndim - 1; d >= 0; d--) {
     j[d] = o % J->oshape[d];
     o /= J->oshape[d];
   }
+  int outside = 0;
   for (int d = 0; d < J->ndim; d++) {
     int64_t centre = j[d] * (int64_t)J->stride[d];
     int64_t a = centre - (J->k[d] - 1) / 2;
     int64_t b = centre + J->k[d] / 2;
+    if (a < 0 || b > J->shape[d] - 1) outside = 1;
     lo[d] = a < 0 ? 0 : a;
     hi[d] = b > J->shape[d] - 1 ? J->shape[d] - 1 : b;
   }
+  return outside;
 }
 
 /* Visit every cell of the box [lo, hi] in C order; returns the flat input
@@ -121,8 +131,25 @@ static int box_next(box_iter *it, int64_t *off) {
 static void one_window(const swo_job *J, int64_t slot) {
   int64_t o = J->idx ? J->idx[slot] : slot;
   int64_t lo[SWO_MAXDIM], hi[SWO_MAXDIM], off;
-  window_of(J, o, lo, hi);
+  const int outside = window_of(J, o, lo, hi);
   box_iter it;
+
+  /* The paper's convention: -2 for a window past an edge or holding a
+   * missing value (<= -999) in either channel. */
+  if (J->border == 1 && (J->c || J->rvx || J->rvy)) {
+    int missing = outside;
+    if (!missing) {
+      box_begin(&it, J, lo, hi);
+      while (box_next(&it, &off))
+        if (value_at(J->dtype, J->x, off) <= -999.0 || value_at(J->dtype, J->y, off) <= -999.0) missing = 1;
+    }
+    if (missing) {
+      if (J->c) J->c[slot] = -2.0;
+      if (J->rvx) J->rvx[slot] = 0.0;
+      if (J->rvy) J->rvy[slot] = 0.0;
+      if (!J->sums) return;
+    }
+  }
 
   /* Exact integer sums (uint16 only): steps 1-3 of Section 1 by brute force. */
   if (J->sums) {
@@ -268,6 +295,22 @@ int swo_corr(int ndim, const int64_t *shape, const int32_t *k, const int32_t *st
   J.c = c;
   J.rvx = relvar_x;
   J.rvy = relvar_y;
+  return run_jobs(&J, nthreads);
+}
+
+/* swo_corr with a border rule: 0 clips the windows to the grid, 1 applies
+ * the paper's -2 convention (see the file header). */
+int swo_corr_border(int ndim, const int64_t *shape, const int32_t *k, const int32_t *stride,
+                    int dtype, const void *x, const void *y, const int64_t *idx, int64_t n_idx,
+                    double *c, double *relvar_x, double *relvar_y, int border, int nthreads) {
+  swo_job J;
+  int rc = setup(&J, ndim, shape, k, stride, dtype, x, y, idx, n_idx);
+  if (rc) return rc;
+  if (border != 0 && border != 1) return -1;
+  J.c = c;
+  J.rvx = relvar_x;
+  J.rvy = relvar_y;
+  J.border = border;
   return run_jobs(&J, nthreads);
 }
 

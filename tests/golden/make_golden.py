@@ -63,6 +63,33 @@ def plane_2d(H=7, W=9, kh=5, kw=3):
                 f.write("%d %d %s\n" % (i, j, s))
 
 
+def plane_2d_paper(H=6, W=9, kh=3, kw=5, miss_x=(3, 4), miss_y=(1, 7)):
+    # The paper's result convention (Section 3, result-set paragraph): a
+    # window reaching past an edge gives -2, and so does a window holding a
+    # missing value (<= -999) in x or y.  Data: x = i + j, y = i - j + 50,
+    # with x[miss_x] = -999 (exactly the threshold) and y[miss_y] = -1000.5.
+    # Every other window is whole (kh x kw cells, no clipping), so the
+    # plane closed form gives c = (vi - vj)/(vi + vj) with vi = (kh^2-1)/12,
+    # vj = (kw^2-1)/12 for all of them.
+    h1, h2, w1, w2 = (kh - 1) // 2, kh // 2, (kw - 1) // 2, kw // 2
+    vi, vj = Fraction(kh * kh - 1, 12), Fraction(kw * kw - 1, 12)
+    cw = (vi - vj) / (vi + vj)
+    with open(os.path.join(HERE, "plane_2d_paper_6x9_k3x5.txt"), "w") as f:
+        f.write("# The paper's -2 convention: x(i,j) = i + j, y(i,j) = i - j + 50 on a %dx%d grid,\n" % (H, W))
+        f.write("# x[%d,%d] = -999, y[%d,%d] = -1000.5 (missing values), window %dx%d, stride 1.\n"
+                % (miss_x + miss_y + (kh, kw)))
+        f.write("# -2 where the window passes an edge or holds a missing cell; else the plane closed\n")
+        f.write("# form (vi - vj)/(vi + vj).  Written by make_golden.py (exact rationals).\n")
+        f.write("# columns: row col c\n")
+        for i in range(H):
+            for j in range(W):
+                edge = i - h1 < 0 or i + h2 > H - 1 or j - w1 < 0 or j + w2 > W - 1
+                holds = any(i - h1 <= r <= i + h2 and j - w1 <= c <= j + w2 for r, c in (miss_x, miss_y))
+                s = "-2" if edge or holds else format(Decimal(cw.numerator) / Decimal(cw.denominator), ".30f")
+                f.write("%d %d %s\n" % (i, j, s))
+
+
 if __name__ == "__main__":
     quadratic_1d()
     plane_2d()
+    plane_2d_paper()

@@ -54,6 +54,15 @@ MUTANTS = [
     ("integer cross sum uses x twice",
      "      syy += b * b;\n      sxy += a * b;",
      "      syy += b * b;\n      sxy += a * a;"),
+    ("missing-value threshold excludes -999 itself",
+     "if (value_at(J->dtype, J->x, off) <= -999.0 || value_at(J->dtype, J->y, off) <= -999.0) missing = 1;",
+     "if (value_at(J->dtype, J->x, off) < -999.0 || value_at(J->dtype, J->y, off) <= -999.0) missing = 1;"),
+    ("missing values looked for in x only",
+     "if (value_at(J->dtype, J->x, off) <= -999.0 || value_at(J->dtype, J->y, off) <= -999.0) missing = 1;",
+     "if (value_at(J->dtype, J->x, off) <= -999.0) missing = 1;"),
+    ("edge test ignores the far edge",
+     "if (a < 0 || b > J->shape[d] - 1) outside = 1;",
+     "if (a < 0) outside = 1;"),
     ("integer sum of y squares drops a term",
      "      syy += b * b;\n      sxy += a * b;\n    }",
      "      syy += b * (b - 1);\n      sxy += a * b;\n    }"),
@@ -63,6 +72,7 @@ MUTANTS = [
 PINS = [
     P.test_golden_quadratic_1d,
     P.test_golden_plane_2d,
+    P.test_golden_plane_2d_paper_convention,
     P.test_plane_2d_transposed_window_differs,
     P.test_even_window_extent,
     lambda: P.test_exact_rational_tiny_grids(1),

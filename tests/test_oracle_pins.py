@@ -56,6 +56,28 @@ def test_golden_plane_2d():
             assert abs(c[int(r), int(col)] - float(val)) < 1e-13
 
 
+def test_golden_plane_2d_paper_convention():
+    """The paper's -2 convention (Section 3, result-set paragraph) on a
+    hand-derived fixture: edges and windows holding a missing value (x at
+    exactly -999, y below it) give -2, the rest the plane closed form; the
+    same values at strided centres."""
+    rows = _read_golden("plane_2d_paper_6x9_k3x5.txt")
+    i, j = np.meshgrid(np.arange(6), np.arange(9), indexing="ij")
+    x = (i + j).astype(np.float32)
+    y = (i - j + 50).astype(np.float32)
+    x[3, 4] = -999.0
+    y[1, 7] = -1000.5
+    want = np.full((6, 9), np.nan)
+    for r, col, val in rows:
+        want[int(r), int(col)] = float(val)
+    c = oracle.corr(x, y, (3, 5), border="paper")
+    assert np.all(np.abs(c - want) < 1e-13)
+    cs = oracle.corr(x, y, (3, 5), (2, 3), border="paper")
+    assert np.all(np.abs(cs - want[::2, ::3]) < 1e-13)
+    # clipped windows are not -2
+    assert not np.any(oracle.corr(x, y, (3, 5)) == -2.0)
+
+
 def test_plane_2d_transposed_window_differs():
     # Swapping the window's row/col extents must flip the sign of the border
     # pattern: catches a transposed k or shape in the index arithmetic.
