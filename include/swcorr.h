@@ -79,7 +79,16 @@ typedef enum {
 
 typedef enum { SWCORR_U16 = 1, SWCORR_F32 = 2 } swcorr_dtype;
 
-typedef enum { SWCORR_BORDER_CLIP = 0 } swcorr_border;
+/* Border rule.
+ *   SWCORR_BORDER_CLIP  : windows are clipped to the grid; n is the number of
+ *                         in-grid cells (a reading: the paper writes -2 there).
+ *   SWCORR_BORDER_PAPER : the paper's result convention (Section 3, the
+ *                         paragraph on the result set): a window that reaches
+ *                         past an edge of the grid gives -2, and so does a
+ *                         window holding a missing value (a value <= -999) in
+ *                         x or in y; other windows as with CLIP (they are whole).
+ *                         Served by the general n-D path. */
+typedef enum { SWCORR_BORDER_CLIP = 0, SWCORR_BORDER_PAPER = 1 } swcorr_border;
 
 enum {
   /* Also write the five window sums (int64: Sx, Sy, Sxx, Syy, Sxy per output,
@@ -93,25 +102,41 @@ enum {
    * other copies and returns, and swcorr_plan_status reports
    * SWCORR_ERR_TIMEOUT; every other item completes normally and the context
    * stays usable.  Outputs of the stalled item are undefined. */
-  SWCORR_FLAG_TEST_STALL = 2u
+  SWCORR_FLAG_TEST_STALL = 2u,
+  /* Ablation of the alternative the paper rejects (Section 1, last
+   * paragraph): window sums from cumulative (summed-area) sums along every
+   * dimension, by inclusion-exclusion over the window's corners, instead of
+   * sliding sums.  Results are identical (the sums are exact modular
+   * integers); only the cost differs.  Served by the general n-D path. */
+  SWCORR_FLAG_SAT = 4u
 };
 
 typedef struct swcorr_plan_s* swcorr_plan;
 
-/* Create a plan for one problem shape.
+/* Create a plan for one problem shape (the windowed correlation of two
+ * equal-size grids, Section 3: "both sets of data must be the same size";
+ * window size and step, Introduction).
  *   out    : receives the plan (set to NULL on failure).
- *   ndim   : 1, 2 or 3.
- *   shape  : ndim extents, each >= 1.
- *   k      : ndim window sizes, each >= 1 (the contiguous dimension's window
- *            k[ndim-1] must be <= 31 for 2-D/3-D).  uint16 windows hold at
- *            most 32768 in-bounds cells (SWCORR_ERR_UNSUPPORTED beyond);
- *            float32 windows of more than 511 cells keep fewer fixed-point
- *            bits per cell (n * 2^bits < 2^31, at most 22 bits).
- *   stride : ndim steps >= 1, or NULL for all ones.
+ *   ndim   : 1 to 8.  1-D, 2-D and 3-D grids with clipped windows run one
+ *            fused kernel (Section 1, steps 1-4 in one pass over HBM); more
+ *            dimensions, the paper's border rule and SWCORR_FLAG_SAT run the
+ *            general path (the steps as separate passes over materialised
+ *            sums, one per dimension: Section 1's n-dimensional
+ *            generalisation, Section 2's parallel phases).
+ *   shape  : ndim extents, each >= 1 and at most 2^31 - 1024.
+ *   k      : ndim window sizes, each >= 1.  The fused 2-D and 3-D kernels take
+ *            windows up to 31 in the contiguous dimension (odd), the 3-D one
+ *            with equal row and column sizes up to 15; uint16 windows hold at
+ *            most 32768 in-bounds cells.  SWCORR_ERR_UNSUPPORTED otherwise.
+ *   stride : ndim steps >= 1, or NULL for all ones (Introduction: "given
+ *            step").
  *   dtype  : SWCORR_U16 or SWCORR_F32 (x and y share it).
- *   border : SWCORR_BORDER_CLIP.
+ *   border : SWCORR_BORDER_CLIP or SWCORR_BORDER_PAPER.
  *   flags  : SWCORR_FLAG_* bits.
- * Host-only work plus device attribute queries; no kernel is launched. */
+ * Host-only work plus device attribute queries and the plan's device
+ * allocations (a status block; the general path's sum buffers, 2 x 5 or 6
+ * int64 per cell); no kernel is launched.  The plan owns its memory until
+ * swcorr_plan_destroy. */
 swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shape,
                                  const int32_t* k, const int32_t* stride, swcorr_dtype dtype,
                                  swcorr_border border, uint32_t flags);

@@ -16,6 +16,7 @@
 #include "../../include/swcorr.h"
 #include "hostapi.h"
 #include "k3d.cuh"
+#include "knd.h"
 #include "launch.h"
 
 using namespace swc;
@@ -273,15 +274,16 @@ swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, con
 
 }  // namespace swc
 
-enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_3D = 4, KIND_BATCHED = 10 };
+enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_3D = 4, KIND_ND = 5, KIND_BATCHED = 10 };
 
 struct swcorr_plan_s {
   int kind = 0;
   int ndim = 0;
-  int64_t shape[3] = {1, 1, 1};
-  int32_t k[3] = {1, 1, 1};
-  int32_t stride[3] = {1, 1, 1};
-  int64_t oshape[3] = {1, 1, 1};
+  int64_t shape[KND_MAXDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  int32_t k[KND_MAXDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  int32_t stride[KND_MAXDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  int64_t oshape[KND_MAXDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  swcorr_border border = SWCORR_BORDER_CLIP;
   swcorr_dtype dtype = SWCORR_U16;
   uint32_t flags = 0;
   DeviceInfo dev;
@@ -297,6 +299,10 @@ struct swcorr_plan_s {
   // 3-D launch
   K3DParams k3{};
   Geo3DInfo g3{};
+  // general n-D path: parameters and its device block (two stream buffers,
+  // scratch)
+  KNDParams kn{};
+  void* d_nd = nullptr;
   // tensor-map cache
   const void* cached_x = nullptr;
   const void* cached_y = nullptr;
@@ -533,6 +539,76 @@ static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, cons
   return SWCORR_OK;
 }
 
+// General n-D path: geometry; its buffers are allocated with the plan.
+static swcorr_status plan_nd(swcorr_plan_s* p) {
+  KNDParams& kn = p->kn;
+  kn.ndim = p->ndim;
+  int64_t cells = 1, outs = 1;
+  uint64_t nmax = 1;
+  for (int d = p->ndim - 1; d >= 0; d--) {
+    kn.shape[d] = p->shape[d];
+    kn.inner[d] = cells;
+    kn.h1[d] = (p->k[d] - 1) / 2;
+    kn.h2[d] = p->k[d] / 2;
+    kn.stride[d] = p->stride[d];
+    kn.oshape[d] = p->oshape[d];
+    if ((double)cells * (double)p->shape[d] > 4.0e12)
+      return fail(SWCORR_ERR_UNSUPPORTED, "grid too large for the general n-D path");
+    cells *= p->shape[d];
+    outs *= p->oshape[d];
+    nmax *= (uint64_t)std::min<int64_t>(p->k[d], p->shape[d]);
+  }
+  kn.ncell = cells;
+  kn.nout = outs;
+  kn.paper = p->border == SWCORR_BORDER_PAPER ? 1 : 0;
+  kn.sat = (p->flags & SWCORR_FLAG_SAT) ? 1 : 0;
+  kn.nstreams = kn.paper ? 6 : 5;
+  kn.is_f32 = p->dtype == SWCORR_F32 ? 1 : 0;
+  if (!kn.is_f32 && nmax > (uint64_t)1 << 30)
+    return fail(SWCORR_ERR_UNSUPPORTED, "uint16 windows of the n-D path are limited to 2^30 cells");
+  // float32: |X| < 2^q per cell and n 2^(2q) < 2^62 keeps the window sums of
+  // squares exact in int64; at most 22 bits (the rounding constant)
+  int q = 22;
+  while (q > 1 && std::ldexp((double)nmax, 2 * q) >= std::ldexp(1.0, 62)) q--;
+  kn.qbits = q;
+  return SWCORR_OK;
+}
+
+static swcorr_status run_nd(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                            const int64_t* out_pitch, int64_t* sums, cudaStream_t st) {
+  KNDParams& kn = p->kn;
+  const int64_t eb = (int64_t)elem_size(p->dtype);
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & (eb - 1))
+    return fail(SWCORR_ERR_ALIGNMENT, "x and y must be aligned to their element size");
+  if (in_pitch) {
+    if (in_pitch[p->ndim - 1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[ndim-1] must be 1");
+    for (int d = 0; d < p->ndim - 1; d++)
+      if (in_pitch[d] < in_pitch[d + 1] * p->shape[d + 1])
+        return fail(SWCORR_ERR_INVALID_ARG, "in_pitch[%d] too small", d);
+  }
+  if (out_pitch) {
+    int64_t want = 1;
+    for (int d = p->ndim - 1; d >= 0; d--) {
+      if (out_pitch[d] != want) return fail(SWCORR_ERR_UNSUPPORTED, "the n-D path writes a contiguous output");
+      want *= p->oshape[d];
+    }
+  }
+  for (int d = 0; d < p->ndim; d++) kn.ipitch[d] = in_pitch ? in_pitch[d] : kn.inner[d];
+  kn.x = x;
+  kn.y = y;
+  kn.out = c;
+  kn.sums = reinterpret_cast<long long*>(sums);
+  unsigned char* base = static_cast<unsigned char*>(p->d_nd);
+  const size_t bytes = (size_t)kn.nstreams * (size_t)kn.ncell * 8;
+  kn.buf[0] = reinterpret_cast<long long*>(base);
+  kn.buf[1] = reinterpret_cast<long long*>(base + bytes);
+  kn.scratch = reinterpret_cast<float*>(base + 2 * bytes);
+  kn.status = p->d_status;
+  cudaError_t e = knd_launch(kn, p->dev.sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "n-D path launch");
+  return SWCORR_OK;
+}
+
 static swcorr_status plan_2d(swcorr_plan_s* p) {
   swcorr_status st = setup_2d(p->dev, p->dtype, (int)p->shape[0], (int)p->shape[1], p->k[0], p->k[1],
                               p->stride[0], p->stride[1], &p->g2, &p->k2, &p->smem, &p->grid, &p->tune);
@@ -577,20 +653,27 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   g_last_error.clear();
   if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (ndim < 1 || ndim > 3) return fail(SWCORR_ERR_UNSUPPORTED, "ndim must be 1, 2 or 3 (got %d)", ndim);
+  if (ndim < 1 || ndim > KND_MAXDIM) return fail(SWCORR_ERR_UNSUPPORTED, "ndim must be 1 to 8 (got %d)", ndim);
   if (!shape || !k) return fail(SWCORR_ERR_INVALID_ARG, "shape and k must not be NULL");
   if (dtype != SWCORR_U16 && dtype != SWCORR_F32) return fail(SWCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
-  if (border != SWCORR_BORDER_CLIP) return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
-  if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL))
+  if (border != SWCORR_BORDER_CLIP && border != SWCORR_BORDER_PAPER)
+    return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
+  if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL | SWCORR_FLAG_SAT))
     return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
+  const bool general = ndim > 3 || border == SWCORR_BORDER_PAPER || (flags & SWCORR_FLAG_SAT);
+  if ((flags & SWCORR_FLAG_TEST_STALL) && general)
+    return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_TEST_STALL applies to 2-D uint16 plans");
   if ((flags & SWCORR_FLAG_TEST_STALL) && !(ndim == 2 && dtype == SWCORR_U16))
     return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_TEST_STALL applies to 2-D uint16 plans");
   if ((flags & SWCORR_FLAG_EMIT_SUMS) && dtype != SWCORR_U16)
     return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_EMIT_SUMS needs uint16 data");
+  if ((flags & SWCORR_FLAG_EMIT_SUMS) && border == SWCORR_BORDER_PAPER)
+    return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_EMIT_SUMS applies to clipped windows");
   swcorr_plan_s tmp;
   tmp.ndim = ndim;
   tmp.dtype = dtype;
   tmp.flags = flags;
+  tmp.border = border;
   for (int d = 0; d < ndim; d++) {
     if (shape[d] < 1) return fail(SWCORR_ERR_INVALID_ARG, "shape[%d] = %lld < 1", d, (long long)shape[d]);
     if (shape[d] > (1ll << 31) - 1024) return fail(SWCORR_ERR_UNSUPPORTED, "shape[%d] too large", d);
@@ -611,7 +694,10 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   } else if (!tune_lookup(tmp.dev.name, "plain", ndim, tmp.k, dtype, &tmp.tune)) {
     tmp.tune = swcorr_tune{};
   }
-  if (ndim == 2) {
+  if (general) {
+    tmp.kind = KIND_ND;
+    st = plan_nd(&tmp);
+  } else if (ndim == 2) {
     tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
     st = plan_2d(&tmp);
   } else if (ndim == 1) {
@@ -640,6 +726,15 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     return cuda_fail(e, "cudaMemset(status)");
   }
   p->k2.status = p->d_status;
+  if (p->kind == KIND_ND) {
+    const size_t bytes = 2 * (size_t)p->kn.nstreams * (size_t)p->kn.ncell * 8 + 64;
+    e = cudaMalloc(&p->d_nd, bytes);
+    if (e != cudaSuccess) {
+      swcorr_plan_destroy(p);
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "n-D stream buffers (%zu B): out of device memory", bytes)
+                                            : cuda_fail(e, "cudaMalloc(n-D buffers)");
+    }
+  }
   *out = p;
   return SWCORR_OK;
 }
@@ -688,6 +783,7 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
   if (!(p->flags & SWCORR_FLAG_EMIT_SUMS)) sums = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   switch (p->kind) {
+    case KIND_ND: return run_nd(p, x, y, in_pitch, c, out_pitch, sums, st);
     case KIND_2D_U16:
     case KIND_2D_F32: return run_2d(p, x, y, in_pitch, c, out_pitch, sums, st);
     case KIND_3D:
@@ -917,7 +1013,7 @@ swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t inner = p->shape[p->ndim - 1];
-  if (p->ndim >= 2 && (inner * (int64_t)elem_size(p->dtype)) % 16 != 0)
+  if (p->kind != KIND_ND && p->ndim >= 2 && (inner * (int64_t)elem_size(p->dtype)) % 16 != 0)
     return fail(SWCORR_ERR_ALIGNMENT, "host runs need rows of a multiple of 16 bytes (got %lld elements)",
                 (long long)inner);
   if (p->kind == KIND_2D_U16 || p->kind == KIND_2D_F32) return run_host_2d_banded(p, x, y, c, st);
@@ -961,6 +1057,7 @@ void swcorr_plan_destroy(swcorr_plan p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->d_batch);
+  cudaFree(p->d_nd);
   cudaFree(p->d_status);
   cudaFree(p->d_x);
   cudaFree(p->d_y);

@@ -17,9 +17,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libswcorr.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NO_DEVICE = range(8)
 U16, F32 = 1, 2
-BORDER_CLIP = 0
+BORDER_CLIP, BORDER_PAPER = 0, 1
+BORDERS = {"clip": BORDER_CLIP, "paper": BORDER_PAPER}
 FLAG_EMIT_SUMS = 1
 FLAG_TEST_STALL = 2
+FLAG_SAT = 4
 
 EXPORTS = ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune", "swcorr_set_tune_file",
            "swcorr_tune_lookup", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",
@@ -172,9 +174,10 @@ class Plan:
     """A plan for one grid shape (swcorr_plan_create / swcorr_run).
 
     tune: None (the tune cache or built-in defaults) or a dict with any of
-    prefetch, tile_rows, ctas_per_sm (swcorr_plan_create_tuned)."""
+    prefetch, tile_rows, ctas_per_sm (swcorr_plan_create_tuned).
+    border: "clip" or "paper" (SWCORR_BORDER_PAPER)."""
 
-    def __init__(self, shape, k, stride=None, dtype="u16", flags=0, tune=None):
+    def __init__(self, shape, k, stride=None, dtype="u16", flags=0, tune=None, border="clip"):
         lib = load()
         self.shape = tuple(int(v) for v in shape)
         nd = len(self.shape)
@@ -188,7 +191,8 @@ class Plan:
         kk, _b = _arr(self.k, ctypes.c_int32)
         ss, _c = _arr(self.stride, ctypes.c_int32)
         t = _tune_struct(tune)
-        _check(lib.swcorr_plan_create_tuned(ctypes.byref(h), nd, shp, kk, ss, self.dtype, BORDER_CLIP, self.flags,
+        self.border = BORDERS[border]
+        _check(lib.swcorr_plan_create_tuned(ctypes.byref(h), nd, shp, kk, ss, self.dtype, self.border, self.flags,
                                             ctypes.byref(t) if t is not None else None))
         self._h = h
 

@@ -47,10 +47,17 @@ def test_argument_errors_without_gpu(lib):
     k = (ctypes.c_int32 * 2)(3, 3)
     bad_k = (ctypes.c_int32 * 2)(0, 3)
     assert lib.swcorr_plan_create(None, 2, shape, k, None, swcorr.U16, 0, 0) == swcorr.ERR_INVALID_ARG
-    assert lib.swcorr_plan_create(ctypes.byref(h), 4, shape, k, None, swcorr.U16, 0, 0) == swcorr.ERR_UNSUPPORTED
+    shape9 = (ctypes.c_int64 * 9)(*([4] * 9))
+    k9 = (ctypes.c_int32 * 9)(*([3] * 9))
+    assert lib.swcorr_plan_create(ctypes.byref(h), 9, shape9, k9, None, swcorr.U16, 0, 0) == swcorr.ERR_UNSUPPORTED
+    assert lib.swcorr_plan_create(ctypes.byref(h), 0, shape9, k9, None, swcorr.U16, 0, 0) == swcorr.ERR_UNSUPPORTED
     assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, bad_k, None, swcorr.U16, 0, 0) == swcorr.ERR_INVALID_ARG
     assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, k, None, 7, 0, 0) == swcorr.ERR_INVALID_ARG
     assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, k, None, swcorr.U16, 3, 0) == swcorr.ERR_INVALID_ARG
+    assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, k, None, swcorr.U16, 0, 64) == swcorr.ERR_INVALID_ARG
+    # sums are defined for clipped windows only
+    assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, k, None, swcorr.U16, swcorr.BORDER_PAPER,
+                                  swcorr.FLAG_EMIT_SUMS) == swcorr.ERR_INVALID_ARG
     assert lib.swcorr_plan_create(ctypes.byref(h), 2, shape, k, None, swcorr.F32, 0, 1) == swcorr.ERR_INVALID_ARG
     assert lib.swcorr_last_error()
     assert lib.swcorr_run(None, None, None, None, None, None, None, None) == swcorr.ERR_INVALID_ARG
