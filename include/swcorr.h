@@ -92,8 +92,10 @@ typedef enum { SWCORR_BORDER_CLIP = 0, SWCORR_BORDER_PAPER = 1 } swcorr_border;
 
 enum {
   /* Also write the five window sums (int64: Sx, Sy, Sxx, Syy, Sxy per output,
-   * output-major) to the sums buffer passed to swcorr_run.  uint16 only; the
-   * sums are the exact integer sums of Section 1, steps 1-3. */
+   * output-major, C order of the output grid) to the sums buffer passed to
+   * swcorr_run: the exact integer sums of Section 1, steps 1-3.  uint16
+   * plans with clipped windows (every kernel: 1-D, 2-D, 3-D and the general
+   * path). */
   SWCORR_FLAG_EMIT_SUMS = 1u,
   /* Test hook for the failure path (not part of the paper's method): in a
    * 2-D uint16 plan whose inputs are read by TMA, the work item of the first

@@ -109,6 +109,18 @@ __device__ __forceinline__ float pearson_exact(const Sums5& s, uint32_t n, float
   return clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
 }
 
+// Debug output of uint16 plans: the exact window sums of output j.
+__device__ __forceinline__ void emit_sums(const K1DParams& p, const Sums5& W, long long j) {
+  if (p.sums != nullptr && j < p.n_out) {
+    long long* s5 = p.sums + 5 * j;
+    s5[0] = (int)W.x;  // below 2^31 for uint16 windows of at most 32768 cells
+    s5[1] = (int)W.y;
+    s5[2] = (long long)W.xx;
+    s5[3] = (long long)W.yy;
+    s5[4] = (long long)W.xy;
+  }
+}
+
 // Recompute the failing outputs (bits of `fail`) of one lane whose first
 // output is j_base, from the chunk's float32 span in shared memory (cell i of
 // the series at gx[i - e0]): a fixed-point map of the lane's own span
@@ -430,6 +442,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
         bool f;
         res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
         fail |= (uint64_t)f << t;
+        if constexpr (!F32) emit_sums(p, W, j_base + t);
         if (t + 1 < M1) {
           const int ei = e_in + t, eo = e_out + t;
           const bool in_ok = ei < ncell;
@@ -442,6 +455,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
         bool f;
         res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
         fail |= (uint64_t)f << t;
+        if constexpr (!F32) emit_sums(p, W, j_base + t);
         if (t + 1 < M1) {
           for (int u = 0; u < p.stride; u++) {
             const int ei = e_in + t * p.stride + u, eo = e_out + t * p.stride + u;

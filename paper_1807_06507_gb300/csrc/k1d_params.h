@@ -25,6 +25,7 @@ struct K1DParams {
   const void* rx;    // the series themselves (always set: float32 windows that
   const void* ry;    //   fail their certificate are recomputed from them)
   float* out;
+  long long* sums;   // optional (uint16): 5 int64 per output, Sx Sy Sxx Syy Sxy
   uint32_t* status;
 };
 

@@ -68,6 +68,7 @@ struct K3DParams {
   long long ipy, ipz;  // input pitches (elements) of a row and of a plane
   int unit_stride;     // sz = sy = sx = 1
   int vec_store;       // output rows 16-byte aligned (unit strides)
+  long long* sums;     // optional (uint16): 5 int64 per output in C order, Sx Sy Sxx Syy Sxy
 };
 
 constexpr int K3_THREADS = 128;
@@ -496,6 +497,17 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
         // a zero variance makes num exactly 0, so 0 * rsqrt(0) = NaN
         return clamp1_nan(i64_to_f32(num) * rsqrtf(fvx * fvy));
       };
+      // debug output of uint16 plans: the exact window sums of output (jz, jy, jx)
+      auto emit = [&](int a, int c, int jz, int jy, int jx) {
+        if (p.sums != nullptr) {
+          long long* s5 = p.sums + 5 * (((long long)jz * p.OY + jy) * p.OX + jx);
+          s5[0] = (int)V0[a][c];  // below 2^31 for uint16 windows of at most 32768 cells
+          s5[1] = (int)V1[a][c];
+          s5[2] = (long long)V2[a][c];
+          s5[3] = (long long)V3[a][c];
+          s5[4] = (long long)V4[a][c];
+        }
+      };
       uint32_t pending = 0;  // bit 4a + c: window whose certificate failed
       int zc_out = 0;
       if (!lane_on) {
@@ -519,6 +531,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
             bool f;
             res[c] = eval(a, c, cz, (uint32_t)(cz * cy * cx), f);
             if (f && xc < p.W) pending |= 1u << (4 * a + c);
+            if (!f32 && xc < p.W) emit(a, c, zc, yc, xc);
           }
           if (p.vec_store && xc0 + 3 < p.W) {
             stg128(orow + xc0, res[0], res[1], res[2], res[3]);
@@ -547,6 +560,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
               bool f;
               orow[xc / p.sx] = eval(a, c, cz, (uint32_t)(cz * cy * cx), f);
               if (f) pending |= 1u << (4 * a + c);
+              if (!f32) emit(a, c, zc / p.sz, yc / p.sy, xc / p.sx);
             }
           }
         }

@@ -787,12 +787,12 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
     case KIND_2D_U16:
     case KIND_2D_F32: return run_2d(p, x, y, in_pitch, c, out_pitch, sums, st);
     case KIND_3D:
-      if (sums) return fail(SWCORR_ERR_UNSUPPORTED, "3-D plans do not emit sums");
+      p->k3.sums = reinterpret_cast<long long*>(sums);
       return run_3d(p, x, y, in_pitch, c, out_pitch, st);
     case KIND_1D:
-      if (sums) return fail(SWCORR_ERR_UNSUPPORTED, "1-D plans do not emit sums");
       if ((in_pitch && in_pitch[0] != 1) || (out_pitch && out_pitch[0] != 1))
         return fail(SWCORR_ERR_UNSUPPORTED, "1-D series must be contiguous");
+      p->k1.sums = reinterpret_cast<long long*>(sums);
       return run_1d(p, x, y, c, st);
   }
   return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);

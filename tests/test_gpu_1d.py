@@ -104,3 +104,23 @@ def test_host_run_1d(sw):
     assert np.array_equal(ch, ref.cpu().numpy(), equal_nan=True)
     p.check_status()
 
+
+
+@pytest.mark.parametrize("n,k,stride", [(40_000, 1001, 1), (20_011, 64, 3), (300_000, 18001, 9), (5_000, 2015, 1)])
+def test_u16_sums_bit_exact(sw, n, k, stride):
+    """The exact window sums (Section 1, steps 1-3) of a 1-D uint16 plan on
+    full-range 16-bit data, up to windows of 18001 cells (the 1-D span of a
+    chunk bounds k by its shared memory)."""
+    rng = np.random.default_rng(n + k)
+    x = rng.integers(0, 65536, n).astype(np.uint16)
+    y = rng.integers(0, 65536, n).astype(np.uint16)
+    x[n // 2: n // 2 + 3000] = 65535
+    p = sw.Plan(x.shape, k, stride, dtype="u16", flags=sw.FLAG_EMIT_SUMS)
+    s = torch.zeros((p.outputs(), 5), dtype=torch.int64, device="cuda")
+    c = p.run(to_dev(x, torch), to_dev(y, torch), sums=s)
+    torch.cuda.synchronize()
+    p.check_status()
+    got = s.cpu().numpy()
+    p.close()
+    assert np.array_equal(got, oracle.sums_u16(x, y, k, stride))
+    score(c.cpu().numpy(), oracle.corr(x, y, k, stride))

@@ -102,3 +102,23 @@ def test_host_run_3d(sw, dtype):
     assert np.array_equal(ch, ref.cpu().numpy(), equal_nan=True)
     p.check_status()
 
+
+
+@pytest.mark.parametrize("shape,k,stride", [((40, 50, 130), (9, 9, 9), None), ((33, 40, 70), (5, 7, 7), (2, 3, 1)),
+                                            ((150, 20, 40), (145, 15, 15), None)])
+def test_u16_sums_bit_exact(sw, shape, k, stride):
+    """The exact window sums of a 3-D uint16 plan on full-range 16-bit data,
+    up to windows of 145 x 15 x 15 = 32625 cells."""
+    rng = np.random.default_rng(sum(shape))
+    x = rng.integers(0, 65536, shape).astype(np.uint16)
+    y = rng.integers(0, 65536, shape).astype(np.uint16)
+    x[:, :5, :9] = 65535
+    p = sw.Plan(x.shape, k, stride, dtype="u16", flags=sw.FLAG_EMIT_SUMS)
+    s = torch.zeros((p.outputs(), 5), dtype=torch.int64, device="cuda")
+    c = p.run(to_dev(x, torch), to_dev(y, torch), sums=s)
+    torch.cuda.synchronize()
+    p.check_status()
+    got = s.cpu().numpy().reshape(p.oshape + (5,))
+    p.close()
+    assert np.array_equal(got, oracle.sums_u16(x, y, k, stride))
+    score(c.cpu().numpy(), oracle.corr(x, y, k, stride))
