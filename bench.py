@@ -200,6 +200,11 @@ def _scored_dc(got, x, y, k, stride, idx):
     return {"max_abs_dc_sampled": dc, "sampled": int(idx.size), "scored": int(sc.sum()), "oracle_nan_kept": nan_ok}
 
 
+def oracle_corr(x, y, k, idx, border):
+    import oracle
+    return oracle.corr(x, y, k, idx=idx, border=border)
+
+
 def secondary(torch, swcorr, workloads, dev, vis, ir):
     """Time the other workload shapes (median launch, inputs resident in HBM)."""
     out = {}
@@ -257,6 +262,47 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
             **_scored_dc(c3.cpu().numpy(), x3, y3, 9, st, idx)}
         del c3, p
     del xd, yd, x3, y3
+
+    # general n-D path (the paper's scheme of one sum pass per dimension over
+    # materialised streams): a 4-D float32 grid, the paper's -2 convention on
+    # the night scene, and the cumulative-sum ablation against sliding sums
+    x4, y4 = workloads.correlated_grid_pair((24, 48, 64, 160))
+    k4 = (3, 5, 5, 7)
+    p = swcorr.Plan(x4.shape, k4, dtype="f32")
+    xd, yd = to(x4), to(y4)
+    c4 = torch.empty(x4.shape, dtype=torch.float32, device=dev)
+    p.fallbacks()
+    t = _events_time(torch, lambda i: p.run(xd, yd, c=c4), 10)
+    p.check_status()
+    idx = rng.integers(0, x4.size, 50_000)
+    out["general_4d_f32_24x48x64x160_k3x5x5x7"] = {
+        "windows_per_s": x4.size / t, "us_per_launch": t * 1e6, "gbs_algorithmic": x4.size * BYTES_PER_WINDOW_F32 / t / 1e9,
+        "recomputed_windows_per_launch": p.fallbacks() / 12.0, **_scored_dc(c4.cpu().numpy(), x4, y4, k4, None, idx)}
+    del xd, yd, c4, p, x4, y4
+    sets = [(to(vis), to(ir), torch.empty(vis.shape, dtype=torch.float32, device=dev)) for _ in range(2)]
+    for name, kw in (("paper_convention_night_u16_k7", dict(border="paper")), ("cumsum_ablation_night_u16_k7",
+                                                                               dict(flags=swcorr.FLAG_SAT))):
+        p = swcorr.Plan(vis.shape, K, dtype="u16", **kw)
+        t = _events_time(torch, lambda i: p.run(*sets[i % 2][:2], c=sets[i % 2][2]), 10)
+        p.check_status()
+        got = sets[0][2].cpu().numpy().ravel()
+        idx = rng.integers(0, vis.size, 50_000)
+        ref = oracle_corr(vis, ir, K, idx, kw.get("border", "clip"))
+        ok = ~np.isnan(ref)
+        out[name] = {"windows_per_s": vis.size / t, "us_per_launch": t * 1e6,
+                     "gbs_algorithmic": vis.size * BYTES_PER_WINDOW_U16 / t / 1e9,
+                     "max_abs_dc_sampled": float(np.max(np.abs(got[idx][ok] - ref[ok]))), "sampled": int(idx.size),
+                     "minus2_mask_equal": bool(np.array_equal(got[idx] == -2.0, ref == -2.0))}
+        p.close()
+    # the same scene through the unfused path with sliding sums (the paper's
+    # scheme), for the two ablations: fusion, and sliding vs cumulative sums
+    p = swcorr.Plan(vis.shape, K, dtype="u16", flags=swcorr.FLAG_UNFUSED)
+    t = _events_time(torch, lambda i: p.run(*sets[i % 2][:2], c=sets[i % 2][2]), 10)
+    p.check_status()
+    out["unfused_sliding_night_u16_k7"] = {"windows_per_s": vis.size / t, "us_per_launch": t * 1e6,
+                                           "gbs_algorithmic": vis.size * BYTES_PER_WINDOW_U16 / t / 1e9}
+    p.close()
+    del sets
 
     # 64 uneven uint16 scenes: one batched launch vs 64 plain launches
     scenes = workloads.batched_scenes(64)

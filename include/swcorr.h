@@ -110,7 +110,13 @@ enum {
    * dimension, by inclusion-exclusion over the window's corners, instead of
    * sliding sums.  Results are identical (the sums are exact modular
    * integers); only the cost differs.  Served by the general n-D path. */
-  SWCORR_FLAG_SAT = 4u
+  SWCORR_FLAG_SAT = 4u,
+  /* Ablation of the fusion: run the general path (the paper's scheme of
+   * Sections 1-2: products and sums materialised in device memory, one pass
+   * per dimension) instead of the fused 1-D/2-D/3-D kernel.  Same results up
+   * to float32 rounding (a float32 grid gets one fixed-point map instead of
+   * one per block); only the cost differs. */
+  SWCORR_FLAG_UNFUSED = 8u
 };
 
 typedef struct swcorr_plan_s* swcorr_plan;

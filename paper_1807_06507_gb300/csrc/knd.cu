@@ -18,8 +18,8 @@
 //    windows that fail it.  All sums are exact (modular) integers.
 //  * Pass along dimension d: sliding sums over the clipped window
 //    [i - floor((k-1)/2), i + floor(k/2)] (outside cells add nothing); one
-//    thread per line (a running sum) for the outer dimensions, one thread
-//    per cell for the contiguous one.  The cumulative-sum ablation instead
+//    thread per segment of a line (a running sum) for the outer dimensions,
+//    one thread per cell for the contiguous one.  The cumulative-sum ablation instead
 //    takes inclusive prefix sums along every dimension (modulo 2^64, still
 //    exact) and forms each window by inclusion-exclusion over its 2^ndim
 //    corners.
@@ -132,30 +132,89 @@ __global__ void __launch_bounds__(kThreads) nd_convert(KNDParams p) {
   if (__any_sync(0xffffffffu, inexact) && (threadIdx.x & 31) == 0) atomicOr(reinterpret_cast<int*>(p.scratch) + 4, 1);
 }
 
-// Pass along an outer dimension d (cells of a line are inner[d] apart): one
-// thread per line, a running sliding sum (or inclusive prefix sum).
+// Pass along an outer dimension d (cells of a line are inner[d] apart).  A
+// line is cut into segments of kSeg cells, one thread each (threads of a
+// warp take neighbouring lines, so their accesses are contiguous): sliding
+// sums start each segment with its first window summed directly; the
+// cumulative-sum ablation takes segment totals, scans them per line, then
+// writes each segment's prefix from its offset.
+constexpr int kSeg = 128;
+
+__device__ __forceinline__ void seg_of(const KNDParams& p, int d, long long t, long long& base, long long& i0,
+                                       long long& i1) {
+  const long long N = p.shape[d], step = p.inner[d];
+  const long long nseg = (N + kSeg - 1) / kSeg, lines = p.ncell / N;
+  const long long line = t % lines, seg = t / lines;
+  base = (line / step) * N * step + line % step;
+  i0 = seg * kSeg;
+  i1 = min(N, i0 + kSeg);
+  (void)nseg;
+}
+
 __global__ void __launch_bounds__(kThreads) nd_pass_lines(KNDParams p, int d, const long long* in, long long* out) {
   const long long N = p.shape[d], step = p.inner[d];
-  const long long lines = p.ncell / N;
+  const long long total = (p.ncell / N) * ((N + kSeg - 1) / kSeg);
   const int h1 = p.h1[d], h2 = p.h2[d];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < lines; t += (long long)gridDim.x * blockDim.x) {
-    const long long base = (t / step) * N * step + t % step;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long base, i0, i1;
+    seg_of(p, d, t, base, i0, i1);
     for (int s = 0; s < p.nstreams; s++) {
       const long long* src = in + s * p.ncell + base;
       long long* dst = out + s * p.ncell + base;
       unsigned long long acc = 0;
-      if (p.sat) {
-        for (long long i = 0; i < N; i++) {
-          acc += (unsigned long long)src[i * step];
-          dst[i * step] = (long long)acc;
-        }
-      } else {
-        for (long long i = 0; i <= min((long long)h2, N - 1); i++) acc += (unsigned long long)src[i * step];
-        for (long long i = 0; i < N; i++) {
-          dst[i * step] = (long long)acc;
-          if (i + h2 + 1 < N) acc += (unsigned long long)src[(i + h2 + 1) * step];
-          if (i - h1 >= 0) acc -= (unsigned long long)src[(i - h1) * step];
-        }
+      for (long long i = max(0ll, i0 - h1); i <= min(N - 1, i0 + (long long)h2); i++) acc += (unsigned long long)src[i * step];
+      for (long long i = i0; i < i1; i++) {
+        dst[i * step] = (long long)acc;
+        if (i + h2 + 1 < N) acc += (unsigned long long)src[(i + h2 + 1) * step];
+        if (i - h1 >= 0) acc -= (unsigned long long)src[(i - h1) * step];
+      }
+    }
+  }
+}
+
+// cumulative sums along an outer dimension: (1) segment totals into seg[]
+__global__ void __launch_bounds__(kThreads) nd_scan_lines_totals(KNDParams p, int d, const long long* in) {
+  const long long N = p.shape[d], step = p.inner[d];
+  const long long total = (p.ncell / N) * ((N + kSeg - 1) / kSeg);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long base, i0, i1;
+    seg_of(p, d, t, base, i0, i1);
+    for (int s = 0; s < p.nstreams; s++) {
+      unsigned long long acc = 0;
+      for (long long i = i0; i < i1; i++) acc += (unsigned long long)in[s * p.ncell + base + i * step];
+      p.segs[s * total + t] = (long long)acc;
+    }
+  }
+}
+
+// (2) exclusive scan of each line's segment totals (one thread per line)
+__global__ void __launch_bounds__(kThreads) nd_scan_lines_offsets(KNDParams p, int d) {
+  const long long N = p.shape[d], lines = p.ncell / N, nseg = (N + kSeg - 1) / kSeg, total = lines * nseg;
+  for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < lines;
+       line += (long long)gridDim.x * blockDim.x)
+    for (int s = 0; s < p.nstreams; s++) {
+      unsigned long long acc = 0;
+      for (long long g = 0; g < nseg; g++) {
+        long long* v = p.segs + s * total + g * lines + line;
+        const unsigned long long tot = (unsigned long long)*v;
+        *v = (long long)acc;
+        acc += tot;
+      }
+    }
+}
+
+// (3) each segment's inclusive prefix from its offset
+__global__ void __launch_bounds__(kThreads) nd_scan_lines_write(KNDParams p, int d, const long long* in, long long* out) {
+  const long long N = p.shape[d], step = p.inner[d];
+  const long long total = (p.ncell / N) * ((N + kSeg - 1) / kSeg);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long base, i0, i1;
+    seg_of(p, d, t, base, i0, i1);
+    for (int s = 0; s < p.nstreams; s++) {
+      unsigned long long acc = (unsigned long long)p.segs[s * total + t];
+      for (long long i = i0; i < i1; i++) {
+        acc += (unsigned long long)in[s * p.ncell + base + i * step];
+        out[s * p.ncell + base + i * step] = (long long)acc;
       }
     }
   }
@@ -344,7 +403,11 @@ cudaError_t knd_launch(const KNDParams& p, int sms, cudaStream_t st) {
   for (int d = 0; d < p.ndim; d++) {
     const long long* in = p.buf[cur];
     long long* out = p.buf[cur ^ 1];
-    if (d < p.ndim - 1)
+    if (d < p.ndim - 1 && p.sat) {
+      nd_scan_lines_totals<<<blocks, kThreads, 0, st>>>(p, d, in);
+      nd_scan_lines_offsets<<<blocks, kThreads, 0, st>>>(p, d);
+      nd_scan_lines_write<<<blocks, kThreads, 0, st>>>(p, d, in, out);
+    } else if (d < p.ndim - 1)
       nd_pass_lines<<<blocks, kThreads, 0, st>>>(p, d, in, out);
     else if (p.sat)
       nd_scan_inner<<<blocks, kThreads, 0, st>>>(p, in, out);

@@ -24,6 +24,7 @@ struct KNDParams {
   float* out;                    // contiguous output
   long long* sums;               // optional: 5 int64 per output (uint16)
   long long* buf[2];             // nstreams x ncell int64 each (ping-pong)
+  long long* segs;               // cumulative-sum ablation: segment totals, nstreams x (ncell / 128 + ncell / N_d)
   float* scratch;                // range of x and y, exactness flag (8 words)
   uint32_t* status;
 };

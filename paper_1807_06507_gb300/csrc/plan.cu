@@ -603,6 +603,7 @@ static swcorr_status run_nd(swcorr_plan_s* p, const void* x, const void* y, cons
   kn.buf[0] = reinterpret_cast<long long*>(base);
   kn.buf[1] = reinterpret_cast<long long*>(base + bytes);
   kn.scratch = reinterpret_cast<float*>(base + 2 * bytes);
+  kn.segs = reinterpret_cast<long long*>(base + 2 * bytes + 64);
   kn.status = p->d_status;
   cudaError_t e = knd_launch(kn, p->dev.sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "n-D path launch");
@@ -658,9 +659,10 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   if (dtype != SWCORR_U16 && dtype != SWCORR_F32) return fail(SWCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
   if (border != SWCORR_BORDER_CLIP && border != SWCORR_BORDER_PAPER)
     return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
-  if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL | SWCORR_FLAG_SAT))
+  if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL | SWCORR_FLAG_SAT | SWCORR_FLAG_UNFUSED))
     return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
-  const bool general = ndim > 3 || border == SWCORR_BORDER_PAPER || (flags & SWCORR_FLAG_SAT);
+  const bool general =
+      ndim > 3 || border == SWCORR_BORDER_PAPER || (flags & (SWCORR_FLAG_SAT | SWCORR_FLAG_UNFUSED));
   if ((flags & SWCORR_FLAG_TEST_STALL) && general)
     return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_TEST_STALL applies to 2-D uint16 plans");
   if ((flags & SWCORR_FLAG_TEST_STALL) && !(ndim == 2 && dtype == SWCORR_U16))
@@ -697,18 +699,25 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   if (general) {
     tmp.kind = KIND_ND;
     st = plan_nd(&tmp);
-  } else if (ndim == 2) {
-    tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
-    st = plan_2d(&tmp);
-  } else if (ndim == 1) {
-    tmp.kind = KIND_1D;
-    st = plan_1d(&tmp);
-  } else if (ndim == 3) {
-    tmp.kind = KIND_3D;
-    st = plan_3d(&tmp);
   } else {
-    st = fail(SWCORR_ERR_UNSUPPORTED, "ndim %d with dtype %s is not provided yet", ndim,
-              dtype == SWCORR_U16 ? "u16" : "f32");
+    if (ndim == 2) {
+      tmp.kind = dtype == SWCORR_U16 ? KIND_2D_U16 : KIND_2D_F32;
+      st = plan_2d(&tmp);
+    } else if (ndim == 1) {
+      tmp.kind = KIND_1D;
+      st = plan_1d(&tmp);
+    } else {
+      tmp.kind = KIND_3D;
+      st = plan_3d(&tmp);
+    }
+    // a window shape the fused kernel has no instance for (even or wide 2-D
+    // widths, unequal or wide 3-D in-plane windows, very long 1-D windows,
+    // uint16 windows beyond 32768 cells) runs on the general path
+    if (st == SWCORR_ERR_UNSUPPORTED && !(flags & SWCORR_FLAG_TEST_STALL)) {
+      g_last_error.clear();
+      tmp.kind = KIND_ND;
+      st = plan_nd(&tmp);
+    }
   }
   if (st != SWCORR_OK) return st;
   swcorr_plan_s* p = new (std::nothrow) swcorr_plan_s(tmp);
@@ -727,7 +736,13 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
   }
   p->k2.status = p->d_status;
   if (p->kind == KIND_ND) {
-    const size_t bytes = 2 * (size_t)p->kn.nstreams * (size_t)p->kn.ncell * 8 + 64;
+    // two stream buffers, scratch, and for the cumulative-sum ablation the
+    // segment totals of the widest pass (at most ncell / 128 + lines per stream)
+    size_t segs = 0;
+    if (p->kn.sat)
+      for (int d = 0; d < p->ndim - 1; d++)
+        segs = std::max(segs, (size_t)((p->kn.ncell / p->kn.shape[d]) * ((p->kn.shape[d] + 127) / 128)));
+    const size_t bytes = 2 * (size_t)p->kn.nstreams * (size_t)p->kn.ncell * 8 + 64 + (size_t)p->kn.nstreams * segs * 8;
     e = cudaMalloc(&p->d_nd, bytes);
     if (e != cudaSuccess) {
       swcorr_plan_destroy(p);

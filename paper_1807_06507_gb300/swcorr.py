@@ -22,6 +22,7 @@ BORDERS = {"clip": BORDER_CLIP, "paper": BORDER_PAPER}
 FLAG_EMIT_SUMS = 1
 FLAG_TEST_STALL = 2
 FLAG_SAT = 4
+FLAG_UNFUSED = 8
 
 EXPORTS = ("swcorr_plan_create", "swcorr_plan_create_tuned", "swcorr_plan_tune", "swcorr_set_tune_file",
            "swcorr_tune_lookup", "swcorr_run", "swcorr_run_host", "swcorr_plan_batched", "swcorr_plan_batched_tuned",

@@ -211,3 +211,13 @@ def batched_scenes(n_scenes=64, seed=seed_for(5), w_range=(1024, 6000), h_range=
         vis, ir = night_scene((h, w), seed=seed + 1000 + i)
         scenes.append(Scene(vis, ir, k, seed + 1000 + i, {"h": h, "w": w}))
     return scenes
+
+
+# ------------------------------------------------------- n-dimensional grids
+def correlated_grid_pair(shape, seed=seed_for(6), rho=0.5):
+    """x ~ N(0,1) iid on a grid of any dimension; y = rho x + N(0,1) noise
+    (float32): the general n-dimensional path's workload."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(shape, dtype=np.float32)
+    y = np.float32(rho) * x + rng.standard_normal(shape, dtype=np.float32)
+    return x, y.astype(np.float32)
