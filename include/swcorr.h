@@ -229,23 +229,32 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
  * not to be run from two host threads at once. */
 swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float* c, void* stream);
 
-/* One scene of a batched plan.  Scenes are 2-D uint16 with square or
- * rectangular windows (k[0] rows, k[1] cols, k[1] <= 31) and stride 1 in this
- * version.  Pointers are device pointers that must stay valid for every
+/* One scene of a batched plan: one 2-D pair of channels of the paper's
+ * all-windows correlation (Section 3), as many scenes of uneven sizes and
+ * window shapes are correlated in one launch.  All scenes of a plan have the
+ * plan's dtype (uint16 or float32); windows are square or rectangular
+ * (k[0] rows, k[1] cols, k[1] odd and <= 31), stride 1, the clipped border.
+ * Pointers are device pointers that must stay valid for every
  * swcorr_run_batched call on the plan. */
 typedef struct {
   int64_t shape[2];     /* rows, cols */
   int32_t k[2];         /* window rows, cols */
   const void* x;        /* device, 16-byte aligned */
   const void* y;        /* device, 16-byte aligned */
-  int64_t in_pitch;     /* elements between rows of x and y (>= cols, multiple of 8) */
+  int64_t in_pitch;     /* elements between rows of x and y (>= cols; pitch in bytes a multiple of 16) */
   float* c;             /* device output, rows x cols */
   int64_t out_pitch;    /* elements between rows of c (>= cols) */
 } swcorr_scene;
 
 /* Plan one persistent launch over all scenes' tiles (a work queue ordered
- * largest-cost first), captured in a CUDA graph on first run.  Copies the
- * scene table; dtype must be SWCORR_U16. */
+ * largest-cost first; one kernel per class of window width), captured in a
+ * CUDA graph on first run.  Copies the scene table; dtype is SWCORR_U16 or
+ * SWCORR_F32 for every scene, with the same numerics as swcorr_run on that
+ * dtype (float32: per-window certificate and exact recomputation).  flags
+ * must be 0.  Errors: SWCORR_ERR_INVALID_ARG (NULL, bad shape or window,
+ * pitch below the row), SWCORR_ERR_ALIGNMENT (base or row pitch not 16-byte
+ * aligned), SWCORR_ERR_UNSUPPORTED (even or > 31 window width, uint16
+ * windows above 32768 cells), SWCORR_ERR_OOM. */
 swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
                                   swcorr_dtype dtype, uint32_t flags);
 
@@ -262,8 +271,9 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream);
 swcorr_status swcorr_plan_status(swcorr_plan p);
 
 /* Diagnostic: number of windows the plan's kernels recomputed through the
- * exact per-window path (uint16 windows whose second-moment sums could not be
- * certified below 2^32) since the last call; reading resets it.  -1 on error. */
+ * exact per-window path since the last call (uint16: windows whose
+ * second-moment sums could not be certified below 2^32; float32: windows
+ * whose fixed-point certificate failed); reading resets it.  -1 on error. */
 int64_t swcorr_plan_fallbacks(swcorr_plan p);
 
 /* No-allocation 2-D uint16 run, for callers that cannot allocate device

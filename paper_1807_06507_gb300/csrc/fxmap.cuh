@@ -244,6 +244,118 @@ static __device__ __noinline__ float fx_box_fp64(const FxBox& b) {
   return (float)fmin(fmax(cv, -1.0), 1.0);
 }
 
+// Warp-cooperative form of fx_box_exact and fx_box_fp64: every lane of a
+// warp calls it with the same box.  The box's cells are dealt to the lanes
+// (lane l takes cells l, l + 32, ... in x-fastest order), so the loads of one
+// step are independent and the window's latency is a few memory round trips
+// instead of n; partial ranges and sums are combined by shuffles (exact:
+// integer sums).  Returns the window's c in every lane and counts it once.
+static __device__ __noinline__ float fx_box_warp(const FxBox& b, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int nxb = b.x1 - b.x0 + 1, nyb = b.y1 - b.y0 + 1;
+  const long long n = (long long)nxb * nyb * (b.z1 - b.z0 + 1);
+  const int dxs = 32 % nxb, dys = 32 / nxb;
+  int x0 = lane % nxb, y0 = (lane / nxb) % nyb, z0 = (lane / nxb) / nyb;
+  auto advance = [&](int& x, int& y, int& z) {
+    x += dxs;
+    y += dys;
+    if (x >= nxb) {
+      x -= nxb;
+      y++;
+    }
+    while (y >= nyb) {
+      y -= nyb;
+      z++;
+    }
+  };
+  auto offset = [&](int x, int y, int z) {
+    return (long long)(b.z0 + z) * b.pz + (long long)(b.y0 + y) * b.py + b.x0 + x;
+  };
+  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+  {
+    int x = x0, y = y0, z = z0;
+    for (long long i = lane; i < n; i += 32) {
+      const long long o = offset(x, y, z);
+      const float u = b.gx[o], v = b.gy[o];
+      xlo = fminf(xlo, u); xhi = fmaxf(xhi, u); ylo = fminf(ylo, v); yhi = fmaxf(yhi, v);
+      advance(x, y, z);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, d));
+    xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, d));
+    ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, d));
+    yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, d));
+  }
+  float c;
+  if (xlo == xhi || ylo == yhi) {  // a constant channel: zero variance, exactly
+    c = __int_as_float(0x7fc00000);
+  } else {
+    const FxWide wx = fx_wide(xlo, xhi, n), wy = fx_wide(ylo, yhi, n);
+    long long S[5] = {0, 0, 0, 0, 0};
+    bool okx = true, oky = true;
+    {
+      int x = x0, y = y0, z = z0;
+      for (long long i = lane; i < n; i += 32) {
+        const long long o = offset(x, y, z);
+        const long long X = fx_wide_quant(b.gx[o], wx, okx), Y = fx_wide_quant(b.gy[o], wy, oky);
+        S[0] += X; S[1] += Y; S[2] += X * X; S[3] += Y * Y; S[4] += X * Y;
+        advance(x, y, z);
+      }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+#pragma unroll
+      for (int t = 0; t < 5; t++) S[t] += __shfl_xor_sync(0xffffffffu, S[t], d);
+    okx = __all_sync(0xffffffffu, okx);
+    oky = __all_sync(0xffffffffu, oky);
+    const __int128 N = n;
+    const __int128 vx = N * S[2] - (__int128)S[0] * S[0];
+    const __int128 vy = N * S[3] - (__int128)S[1] * S[1];
+    const __int128 num = N * S[4] - (__int128)S[0] * S[1];
+    if (fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, okx ? 0.0f : 0.5f, oky ? 0.0f : 0.5f)) {
+      c = fx_pearson128(num, vx, vy);
+    } else {  // FP64, two passes (the classical formula, Introduction)
+      double sx = 0.0, sy = 0.0;
+      {
+        int x = x0, y = y0, z = z0;
+        for (long long i = lane; i < n; i += 32) {
+          const long long o = offset(x, y, z);
+          sx += b.gx[o];
+          sy += b.gy[o];
+          advance(x, y, z);
+        }
+      }
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, d);
+        sy += __shfl_xor_sync(0xffffffffu, sy, d);
+      }
+      const double mx = sx / (double)n, my = sy / (double)n;
+      double sxx = 0.0, syy = 0.0, sxy = 0.0;
+      {
+        int x = x0, y = y0, z = z0;
+        for (long long i = lane; i < n; i += 32) {
+          const long long o = offset(x, y, z);
+          const double u = (double)b.gx[o] - mx, v = (double)b.gy[o] - my;
+          sxx += u * u; syy += v * v; sxy += u * v;
+          advance(x, y, z);
+        }
+      }
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        sxx += __shfl_xor_sync(0xffffffffu, sxx, d);
+        syy += __shfl_xor_sync(0xffffffffu, syy, d);
+        sxy += __shfl_xor_sync(0xffffffffu, sxy, d);
+      }
+      c = (float)fmin(fmax(sxy / sqrt(sxx * syy), -1.0), 1.0);
+    }
+  }
+  if (lane == 0 && status) atomicAdd(status + ST_FALLBACK, 1u);
+  return c;
+}
+
 // Recompute one window exactly (window-local map, else FP64) and count it.
 static __device__ __noinline__ float fx_recompute(const FxBox& b, uint32_t* status) {
   float c;

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid
   rg.lx = rg.ry + (size_t)p.NR * G::RWS;
   rg.ly = rg.lx + (size_t)p.NR * G::RWS;
   rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
-  __shared__ uint64_t pend[kPend2D];  // windows whose quick certificate test failed
+  __shared__ uint32_t pend[kPend2D];  // windows the lane re-march could not certify
   __shared__ int npend;
   rg.pend = pend;
   rg.npend = &npend;

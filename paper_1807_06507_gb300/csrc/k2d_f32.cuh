@@ -33,10 +33,14 @@
 //    rounding bound, |dc| <= rho n (1/sqrt(vx) + 1/sqrt(vy)) + 7e-7.  The
 //    common case passes a one-comparison-per-channel test (lanes of integer
 //    data on a grid step of at most 1 convert exactly, rho = 0: nothing to
-//    test).  A window that does not pass is listed; after the item, each lane
-//    with listed windows determines whether its values convert exactly, and
-//    the listed windows of the other lanes are recomputed from their own
-//    cells and stored over the fixed-point results.
+//    test).  A window that does not pass flags its lane.  After the item,
+//    each flagged lane determines whether its values convert exactly (then
+//    its results stand); the others march their item again from L2 with a
+//    finer map of the same range (up to 26 bits, 64-bit sums, Eq. 2 in
+//    128-bit integers), which certifies the windows of ordinary float data
+//    whose spread is small next to the lane's range.  Windows that still
+//    fail (a value orders of magnitude above its neighbours in the lane's
+//    columns) are recomputed from their own cells by the whole warp at once.
 #pragma once
 
 #include <type_traits>
@@ -73,20 +77,17 @@ struct Ring2DF {
   uint64_t* bar;  // [NR]
   int NR;
   int PF;
-  uint64_t* pend; // windows whose quick certificate test failed: row << 8 | lane << 3 | column
+  uint32_t* pend; // windows the lane re-march could not certify: (row - j0) << 8 | lane << 3 | column
   int* npend;     //   (at most kPend2D per item; the count may run past it)
 };
 
-constexpr int kPend2D = 256;
+constexpr int kPend2D = 512;
 
-// Fix-up of one output row of a lane: every window flagged in `fail`
-// (bit c: centre column cl + c) is recomputed from its own cells
-// (fx_recompute) and stored over the fixed-point result.
 struct FixScene2D {  // the fields of a scene the fix-up reads (passed by value)
   const float* gx;
   const float* gy;
   long long in_pitch;
-  int H, W, h1, h2, kw, sx, sy;
+  int H, W, h1, h2, kh, kw, sx, sy;
 };
 
 // Whether every in-grid value of a lane's item (rows [r0, r1), the lane's
@@ -121,10 +122,11 @@ static __device__ __noinline__ bool lane_exact_2d(const float* gx, const float* 
   return false;
 }
 
-// Recompute the window of centre (rc, cc) from its cells (fx_recompute) and
-// store it over the fixed-point result.
-static __device__ __noinline__ void fixup_window_2d(const FixScene2D& sc, float* out, long long out_pitch, int jr,
-                                                    int cc, uint32_t* status) {
+// Recompute the window of centre (jr sy, cc) from its cells, the whole warp
+// together (fx_box_warp), and store it over the earlier result.
+static __device__ __noinline__ void fix_window_warp_2d(const FixScene2D& sc, float* out, long long out_pitch, int jr,
+                                                       int cc) {
+  // (arguments are the same in every lane)
   if (cc >= sc.W || (sc.sx != 1 && cc % sc.sx != 0)) return;
   const int rc = jr * sc.sy, w1 = (sc.kw - 1) / 2, w2 = sc.kw / 2;
   FxBox b;
@@ -137,33 +139,31 @@ static __device__ __noinline__ void fixup_window_2d(const FixScene2D& sc, float*
   b.y1 = min(rc + sc.h2, sc.H - 1);
   b.x0 = max(cc - w1, 0);
   b.x1 = min(cc + w2, sc.W - 1);
-  out[(long long)jr * out_pitch + (sc.sx == 1 ? cc : cc / sc.sx)] = fx_recompute(b, status);
+  const float c = fx_box_warp(b, nullptr);
+  if ((threadIdx.x & 31) == 0) out[(long long)jr * out_pitch + (sc.sx == 1 ? cc : cc / sc.sx)] = c;
 }
 
-// The failing windows of a work item, after its row march (the whole warp
-// calls it): each lane with a listed window (or an overflow) learns whether
-// its values convert exactly; the listed windows of the other lanes are
-// recomputed by the warp in parallel, and a lane that overflowed the list
-// recomputes all its windows (output rows [j0, j1), columns cl + 0..M-1).
-template <int M, int NCOL>
-static __device__ __noinline__ void fixup_item_2d(FixScene2D sc, float* out, long long out_pitch, const uint64_t* pend,
-                                                  int n, bool need, bool ovf, int exact_state, int r0, int r1, int cl,
-                                                  int w1, int j0, int j1, FxMap qx, FxMap qy, uint32_t* status) {
+// The windows the second tier could not certify (the whole warp calls it):
+// each listed window, then every window of a lane whose list overflowed, is
+// recomputed by the whole warp from its own cells (fx_box_warp).
+template <int M>
+static __device__ __noinline__ void fix_listed_2d(FixScene2D sc, float* out, long long out_pitch, const uint32_t* pend,
+                                                  int npend, bool ovf, int cl, int j0, int j1, uint32_t* status) {
   const int lane = threadIdx.x & 31;
-  if (need && exact_state < 0)
-    exact_state = lane_exact_2d<NCOL>(sc.gx, sc.gy, sc.in_pitch, r0, r1, cl - w1, max(0, w1 - cl),
-                                      min(NCOL, sc.W - (cl - w1)), qx, qy)
-                      ? 1
-                      : 0;
-  const uint32_t inexact = __ballot_sync(0xffffffffu, need && exact_state == 0);
-  for (int i = lane; i < min(n, kPend2D); i += 32) {
-    const uint64_t e = pend[i];
+  const int n = min(npend, kPend2D);
+  for (int i = 0; i < n; i++) {
+    const uint32_t e = pend[i];
     const int l = (int)(e >> 3) & 31;
-    if ((inexact >> l) & 1u) fixup_window_2d(sc, out, out_pitch, (int)(e >> 8), cl - M * lane + M * l + (int)(e & 7), status);
+    fix_window_warp_2d(sc, out, out_pitch, j0 + (int)(e >> 8), cl - M * lane + M * l + (int)(e & 7));
   }
-  if (ovf && exact_state == 0)
+  uint32_t om = __ballot_sync(0xffffffffu, ovf);
+  while (om) {
+    const int l = __ffs(om) - 1;
+    om &= om - 1;
     for (int jr = j0; jr < j1; jr++)
-      for (int c = 0; c < M; c++) fixup_window_2d(sc, out, out_pitch, jr, cl + c, status);
+      for (int c = 0; c < M; c++) fix_window_warp_2d(sc, out, out_pitch, jr, cl - M * lane + M * l + c);
+  }
+  if (lane == 0 && n > 0) atomicAdd(status + ST_FALLBACK, (uint32_t)n);
 }
 
 template <int M, int KW, bool TMA>
@@ -310,9 +310,7 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   // lane exactness: -1 not yet known, 0 no, 1 yes (integers on a grid step of
   // at most 1: x - m and (x - m) s are exact)
   const int exact_state = (allint && qx.s >= 1.0f && qy.s >= 1.0f) ? 1 : -1;
-  bool need = false, ovf = false;  // the lane listed failing windows; its list overflowed
-  if (lane == 0) *rg.npend = 0;
-  __syncwarp();
+  bool need = false;  // a window of the lane failed its quick certificate test
   float Kx, Ky;  // quick certificate thresholds, fixed for the item
   {
     const float nmax = (float)(sc.kh * KW);
@@ -440,18 +438,9 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
           if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) orow[sc.sx == 1 ? cc : cc / sc.sx] = res[c];
         }
       }
-      // rare: list the failing windows (recomputed after the item, unless the
-      // lane converts exactly)
-      if (fail != 0u && exact_state != 1) {
-        for (uint32_t f = fail; f; f &= f - 1) {
-          const int k = atomicAdd(rg.npend, 1);
-          if (k < kPend2D)
-            rg.pend[k] = ((uint64_t)jr << 8) | ((uint64_t)lane << 3) | (uint64_t)(__ffs(f) - 1);
-          else
-            ovf = true;
-        }
-        need = true;
-      }
+      // rare: a window the item map cannot certify (the lane's windows are
+      // recomputed after the item, unless the lane converts exactly)
+      if (fail != 0u && exact_state != 1) need = true;
       if (lane_border) {
         // restore the running sums for the next rows
 #pragma unroll
@@ -471,11 +460,145 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   (void)seq0;
   if (!ok) return false;
   __syncwarp();
+
+  // ---- pass 3 (second tier): lanes whose item map left a window
+  // uncertified and whose values do not all convert exactly march the item
+  // again through the ring with a finer map of the same range, fx_wide (up to
+  // 26 bits, 64-bit sums; values on the grid exact, others within 1/2), and
+  // evaluate Eq. 2 in 128-bit integers.  Cells outside the grid are absent
+  // (X = 0, not counted).  Two passes of M/2 windows each (the 64-bit running
+  // sums of all M windows would not fit the registers).  Every window of the
+  // lane is rewritten; those that still fail are listed for the warp.
+  bool redo = false;
   if (__any_sync(0xffffffffu, need)) {
-    const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, KW, sc.sx,
-                        sc.sy};
-    fixup_item_2d<M, G::NCOL>(fs, sc.out, sc.out_pitch, rg.pend, *rg.npend, need, ovf, exact_state, max(t0, 0),
-                              min(t0 + nrows, sc.H), cl, G::W1, j0, j1, qx, qy, status);
+    const bool exact = exact_state == 1 ||
+                       (need && exact_state < 0 &&
+                        lane_exact_2d<G::NCOL>((const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, max(t0, 0),
+                                               min(t0 + nrows, sc.H), cl - G::W1, e_lo, e_hi, qx, qy));
+    // a channel constant over the lane's cells makes every window's variance
+    // exactly zero: the item map's results (NaN) stand
+    redo = need && !exact && xlo < xhi && ylo < yhi;
+  }
+  if (__any_sync(0xffffffffu, redo)) {
+    if (lane == 0) *rg.npend = 0;
+    __syncwarp();
+    const long long nmax = (long long)sc.kh * KW;
+    const FxWide wx = fx_wide(xlo, xhi, nmax), wy = fx_wide(ylo, yhi, nmax);
+    bool ongx = true, ongy = true;  // every value read so far lies on its channel's grid
+    bool ovf = false;
+    uint32_t count = 0;
+    auto redo_pass = [&](auto half_tag) -> bool {
+      constexpr int HALF = decltype(half_tag)::value;
+      constexpr int MH = M / 2, NC = MH + KW - 1, EB = HALF * MH;  // lane columns [EB, EB + NC)
+      constexpr int HB = (G::E0 + EB) / 4, HE = (G::E0 + EB + NC - 1) / 4 + 1;
+      unsigned long long V[MH][5];
+#pragma unroll
+      for (int c = 0; c < MH; c++)
+#pragma unroll
+        for (int t = 0; t < 5; t++) V[c][t] = 0ull;
+      int until_out = sc.kh - 1;
+      int jr = j0;
+      return stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
+        constexpr bool has_leave = decltype(leave_tag)::value;
+        if (redo) {
+          const int te = t0 + i, tl = te - sc.kh;
+          const bool e_ok = te >= 0 && te < sc.H;
+          const bool l_ok = has_leave && tl >= 0 && tl < sc.H;
+          const float* pxe = lane_ptr(rg.rx, s);
+          const float* pye = lane_ptr(rg.ry, s);
+          const float* pxl = lane_ptr(rg.lx, s);
+          const float* pyl = lane_ptr(rg.ly, s);
+          unsigned long long P[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+          unsigned long long Ps[MH > 1 ? MH - 1 : 1][5];
+#pragma unroll
+          for (int h = HB; h < HE; h++) {
+            const float4 a = *reinterpret_cast<const float4*>(pxe + 4 * h);
+            const float4 b = *reinterpret_cast<const float4*>(pye + 4 * h);
+            float4 al = make_float4(0.f, 0.f, 0.f, 0.f), bl = al;
+            if constexpr (has_leave) {
+              al = *reinterpret_cast<const float4*>(pxl + 4 * h);
+              bl = *reinterpret_cast<const float4*>(pyl + 4 * h);
+            }
+            const float xa[4] = {a.x, a.y, a.z, a.w}, ya[4] = {b.x, b.y, b.z, b.w};
+            const float xla[4] = {al.x, al.y, al.z, al.w}, yla[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              const int e = 4 * h + u - G::E0;
+              if (e < EB || e >= EB + NC) continue;
+              const bool cok = e >= e_lo && e < e_hi;
+              long long Xe = 0, Ye = 0, Xl = 0, Yl = 0;
+              if (e_ok && cok) {
+                Xe = fx_wide_quant(xa[u], wx, ongx);
+                Ye = fx_wide_quant(ya[u], wy, ongy);
+              }
+              if (l_ok && cok) {
+                Xl = fx_wide_quant(xla[u], wx, ongx);
+                Yl = fx_wide_quant(yla[u], wy, ongy);
+              }
+              // |X| < 2^26 (1 + 2^-6) + 1: differences, sums and their
+              // products fit 32 x 32 -> 64-bit multiplies
+              const int D = (int)(Xe - Xl), S = (int)(Xe + Xl), Dy = (int)(Ye - Yl), Sy = (int)(Ye + Yl);
+              P[0] += (unsigned long long)(long long)D;
+              P[1] += (unsigned long long)(long long)Dy;
+              P[2] += (unsigned long long)((long long)D * S);
+              P[3] += (unsigned long long)((long long)Dy * Sy);
+              P[4] += (unsigned long long)((long long)D * (int)Ye + (long long)(int)Xl * Dy);
+              const int j = e - EB;
+              if (j >= KW - 1) {
+                const int c = j - (KW - 1);
+#pragma unroll
+                for (int t = 0; t < 5; t++) V[c][t] += P[t] - (c >= 1 ? Ps[c - 1][t] : 0ull);
+              }
+              if (j <= MH - 2) {
+#pragma unroll
+                for (int t = 0; t < 5; t++) Ps[j][t] = P[t];
+              }
+            }
+          }
+        }
+        if (until_out == 0) {
+          until_out = sc.sy;
+          if (redo) {
+            const int rc = jr * sc.sy;
+            const long long cnt_r = min(rc + sc.h2, sc.H - 1) - max(rc - sc.h1, 0) + 1;
+            float* orow = sc.out + (long long)jr * sc.out_pitch;
+#pragma unroll
+            for (int c = 0; c < MH; c++) {
+              const int cc = cl + EB + c;
+              if (cc < sc.W && (sc.sx == 1 || cc % sc.sx == 0)) {
+                const long long n = cnt_r * (min(cc + G::W2, sc.W - 1) - max(cc - G::W1, 0) + 1);
+                const long long s0 = (long long)V[c][0], s1 = (long long)V[c][1];
+                const __int128 vx = (__int128)n * (long long)V[c][2] - (__int128)s0 * s0;
+                const __int128 vy = (__int128)n * (long long)V[c][3] - (__int128)s1 * s1;
+                const __int128 num = (__int128)n * (long long)V[c][4] - (__int128)s0 * s1;
+                float r = __int_as_float(0x7fc00000);
+                if (fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, ongx ? 0.0f : 0.5f,
+                                 ongy ? 0.0f : 0.5f)) {
+                  r = fx_pearson128(num, vx, vy);
+                } else {
+                  const int k = atomicAdd(rg.npend, 1);
+                  if (k < kPend2D)
+                    rg.pend[k] = ((uint32_t)(jr - j0) << 8) | ((uint32_t)lane << 3) | (uint32_t)(EB + c);
+                  else
+                    ovf = true;
+                }
+                orow[sc.sx == 1 ? cc : cc / sc.sx] = r;
+                count++;
+              }
+            }
+          }
+          jr++;
+        }
+        until_out--;
+      });
+    };
+    if (!redo_pass(std::integral_constant<int, 0>{})) return false;
+    if (!redo_pass(std::integral_constant<int, 1>{})) return false;
+    if (count) atomicAdd(status + ST_FALLBACK, count);
+    __syncwarp();
+    const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, sc.kh, KW,
+                        sc.sx, sc.sy};
+    fix_listed_2d<M>(fs, sc.out, sc.out_pitch, rg.pend, *rg.npend, ovf, cl, j0, j1, status);
   }
   return true;
 }

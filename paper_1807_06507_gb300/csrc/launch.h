@@ -37,6 +37,12 @@ const void* kbatched_kernel_ptr(int cls);
 cudaError_t kbatched_prepare();
 cudaError_t kbatched_launch(const KBatchParams& p, int cls, int grid, size_t smem, cudaStream_t st);
 
+// Batched 2-D float32: ring row stride, kernel (occupancy queries), launch.
+int kbatched_f32_ring_row();
+const void* kbatched_f32_kernel_ptr(int cls);
+cudaError_t kbatched_f32_prepare();
+cudaError_t kbatched_f32_launch(const KBatchParams& p, int cls, int grid, size_t smem, cudaStream_t st);
+
 // 3-D (uint16 or float32), square in-plane windows ky = kx = k.
 struct Geo3DInfo {
   int TY, TX, TYI, BXW, XH, VSP;

@@ -1103,7 +1103,8 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   if (!out) return fail(SWCORR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!scenes || n_scenes < 1) return fail(SWCORR_ERR_INVALID_ARG, "need at least one scene");
-  if (dtype != SWCORR_U16) return fail(SWCORR_ERR_UNSUPPORTED, "batched plans take uint16 scenes");
+  if (dtype != SWCORR_U16 && dtype != SWCORR_F32) return fail(SWCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  const bool f32 = dtype == SWCORR_F32;
   if (flags != 0) return fail(SWCORR_ERR_INVALID_ARG, "batched plans take no flags");
   swcorr_status st = tune_check(tune);
   if (st != SWCORR_OK) return st;
@@ -1117,7 +1118,7 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
     tn = swcorr_tune{};
   }
   const int rows_min = tn.tile_rows > 0 ? tn.tile_rows : 64;
-  cudaError_t e = kbatched_prepare();
+  cudaError_t e = f32 ? kbatched_f32_prepare() : kbatched_prepare();
   if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
 
   // per-scene set-up on the host
@@ -1130,16 +1131,16 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
     if (s.shape[0] < 1 || s.shape[1] < 1 || s.shape[0] > (1ll << 31) - 1024 || s.shape[1] > (1ll << 31) - 1024)
       return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad shape", i);
     if (s.k[0] < 1 || s.k[1] < 1) return fail(SWCORR_ERR_INVALID_ARG, "scene %d: bad window", i);
-    if ((uint64_t)std::min<int64_t>(s.k[0], s.shape[0]) * (uint64_t)std::min<int64_t>(s.k[1], s.shape[1]) > kMaxU16Cells)
+    if (!f32 && (uint64_t)std::min<int64_t>(s.k[0], s.shape[0]) * (uint64_t)std::min<int64_t>(s.k[1], s.shape[1]) > kMaxU16Cells)
       return fail(SWCORR_ERR_UNSUPPORTED, "scene %d: uint16 windows are limited to %llu in-bounds cells", i,
                   (unsigned long long)kMaxU16Cells);
     Geo2DInfo g;
-    if (!k2d_u16_geometry(s.k[1], &g) || g.M != 8)
+    if (!(f32 ? k2d_f32_geometry(s.k[1], &g) : k2d_u16_geometry(s.k[1], &g)) || g.M != 8)
       return fail(SWCORR_ERR_UNSUPPORTED, "scene %d: window width %d has no kernel instance (1..31 odd)", i, s.k[1]);
     if (!s.x || !s.y || !s.c) return fail(SWCORR_ERR_INVALID_ARG, "scene %d: NULL pointer", i);
     if (s.in_pitch < s.shape[1] || s.out_pitch < s.shape[1])
       return fail(SWCORR_ERR_INVALID_ARG, "scene %d: pitch smaller than the row", i);
-    if (((reinterpret_cast<uintptr_t>(s.x) | reinterpret_cast<uintptr_t>(s.y)) & 15) || (s.in_pitch * 2) % 16)
+    if (((reinterpret_cast<uintptr_t>(s.x) | reinterpret_cast<uintptr_t>(s.y)) & 15) || (s.in_pitch * (f32 ? 4 : 2)) % 16)
       return fail(SWCORR_ERR_ALIGNMENT, "scene %d: batched inputs need 16-byte aligned bases and row pitches", i);
     Scene2D& q = sc[i];
     q.H = (int)s.shape[0];
@@ -1163,12 +1164,15 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
     q.out_pitch = s.out_pitch;
     q.sums = nullptr;
     q.vec_store = ((reinterpret_cast<uintptr_t>(s.c) & 15) == 0 && (s.out_pitch % 4) == 0) ? 1 : 0;
-    q.wide = (n > 64 || q.kw > 9) ? 1 : 0;  // the batched kernel has 32-bit bodies for kw <= 9 only
-    st = encode_2d(&maps[4 * i + 0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.x, q.W, q.H, s.in_pitch, 256);
-    if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.y, q.W, q.H, s.in_pitch, 256);
+    q.wide = (!f32 && (n > 64 || q.kw > 9)) ? 1 : 0;  // the batched kernel has 32-bit bodies for kw <= 9 only
+    q.qbits = f32_qbits(n);
+    const CUtensorMapDataType tdt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const int eb = f32 ? 4 : 2;
+    st = encode_2d(&maps[4 * i + 0], tdt, eb, s.x, q.W, q.H, s.in_pitch, 256);
+    if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 1], tdt, eb, s.y, q.W, q.H, s.in_pitch, 256);
     if (st == SWCORR_OK && g.TAIL > 0) {
-      st = encode_2d(&maps[4 * i + 2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.x, q.W, q.H, s.in_pitch, g.TAIL);
-      if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 3], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s.y, q.W, q.H, s.in_pitch, g.TAIL);
+      st = encode_2d(&maps[4 * i + 2], tdt, eb, s.x, q.W, q.H, s.in_pitch, g.TAIL);
+      if (st == SWCORR_OK) st = encode_2d(&maps[4 * i + 3], tdt, eb, s.y, q.W, q.H, s.in_pitch, g.TAIL);
     }
     if (st != SWCORR_OK) return st;
     cost[i] = (double)(q.TJ + q.kh - 1) * (8 + q.kw - 1 + 16);
@@ -1180,7 +1184,10 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   // items grouped by kernel class (32-bit engine; 64-bit up to 17 columns;
   // 64-bit above), one launch each
-  auto cls_of = [&](int i) { return sc[i].wide == 0 ? 0 : (sc[i].kw <= 17 ? 1 : 2); };
+  auto cls_of = [&](int i) {
+    if (f32) return sc[i].kw <= 9 ? 0 : (sc[i].kw <= 17 ? 1 : 2);
+    return sc[i].wide == 0 ? 0 : (sc[i].kw <= 17 ? 1 : 2);
+  };
   std::vector<BatchItem> items;
   size_t cls_start[4] = {0, 0, 0, 0};
   for (int cls = 0; cls < 3; cls++) {
@@ -1231,7 +1238,8 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
       (e = cudaMemset(p->d_status, 0, ST_WORDS * sizeof(uint32_t))) != cudaSuccess)
     return cleanup(cuda_fail(e, "batched plan upload"));
   const int PF = tn.prefetch > 0 ? tn.prefetch : 4;
-  p->smem = (size_t)4 * (PF + 1) * kbatched_ring_row() * 2 + (size_t)(PF + 1) * 8;
+  p->smem = f32 ? (size_t)4 * (PF + 1) * kbatched_f32_ring_row() * 4 + (size_t)(PF + 1) * 8
+                : (size_t)4 * (PF + 1) * kbatched_ring_row() * 2 + (size_t)(PF + 1) * 8;
   int per_sm_max = 0;
   for (int cls = 0; cls < 3; cls++) {
     KBatchParams& kb = p->kbs[cls];
@@ -1243,7 +1251,8 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
     kb.counter = reinterpret_cast<uint32_t*>(base + ctr_off) + cls;
     kb.status = p->d_status;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbatched_kernel_ptr(cls), 32, p->smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32 ? kbatched_f32_kernel_ptr(cls) : kbatched_kernel_ptr(cls),
+                                                      32, p->smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 8;
     if (tn.ctas_per_sm > 0) per_sm = std::min(per_sm, tn.ctas_per_sm);
@@ -1271,7 +1280,9 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
     cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, 3 * sizeof(uint32_t), p->cap_stream);
     cudaError_t e2 = cudaSuccess;
     for (int cls = 0; cls < 3 && e2 == cudaSuccess; cls++)
-      if (p->kbs[cls].n_items > 0) e2 = kbatched_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream);
+      if (p->kbs[cls].n_items > 0)
+        e2 = p->dtype == SWCORR_F32 ? kbatched_f32_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream)
+                                    : kbatched_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream);
     e = cudaStreamEndCapture(p->cap_stream, &p->graph);
     if (e1 != cudaSuccess) return cuda_fail(e1, "capture counter reset");
     if (e2 != cudaSuccess) return cuda_fail(e2, "capture batched kernel");

@@ -267,12 +267,18 @@ class Plan:
 
 
 class BatchedPlan:
-    """One persistent launch over many 2-D uint16 scenes (swcorr_plan_batched)."""
+    """One persistent launch over many 2-D scenes of one dtype, uint16 or
+    float32 (swcorr_plan_batched)."""
 
     def __init__(self, scenes, flags=0, tune=None):
-        """scenes: list of (x, y, c, (kh, kw)) with CUDA tensors; x/y rows may be
-        padded (strided views with unit last stride).  tune: as for Plan."""
+        """scenes: list of (x, y, c, (kh, kw)) with CUDA tensors (all uint16,
+        carried as int16, or all float32); x/y rows may be padded (strided
+        views with unit last stride).  tune: as for Plan."""
         lib = load()
+        dts = {str(t.dtype) for sc in scenes for t in sc[:2]}
+        if len(dts) != 1:
+            raise ValueError(f"a batched plan takes scenes of one dtype, got {sorted(dts)}")
+        dt = F32 if dts == {"torch.float32"} else U16
         arr = (SceneStruct * len(scenes))()
         self._keep = []
         for i, (x, y, c, k) in enumerate(scenes):
@@ -286,7 +292,7 @@ class BatchedPlan:
             self._keep.append((x, y, c))
         h = ctypes.c_void_p()
         t = _tune_struct(tune)
-        _check(lib.swcorr_plan_batched_tuned(ctypes.byref(h), arr, len(scenes), U16, int(flags),
+        _check(lib.swcorr_plan_batched_tuned(ctypes.byref(h), arr, len(scenes), dt, int(flags),
                                              ctypes.byref(t) if t is not None else None))
         self._h = h
 

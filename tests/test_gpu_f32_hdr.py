@@ -146,3 +146,29 @@ def test_2d_integer_data_converts_exactly(sw):
     c, fb = run(sw, x, y, 7)
     check(c, x, y, 7)
     assert fb == 0
+
+
+@pytest.mark.parametrize("k", [7, (31, 31), (9, 3)])
+def test_2d_off_integer_night_scene(sw, k):
+    """A night scene scaled off the integers (lights thousands of times the
+    dark level): the lane maps leave most dark windows uncertified, so the
+    lanes' second tier (the finer re-march) carries them."""
+    vis, ir = W.night_scene((300, 700), seed=17)
+    x, y = vis.astype(np.float32) * np.float32(0.37), ir.astype(np.float32)
+    c, fb = run(sw, x, y, k)
+    m, n_sc, _ = check(c, x, y, k)
+    assert n_sc > 150_000
+    assert fb > 0
+
+
+def test_2d_smooth_radiance_field(sw):
+    """A smooth log-normal field with 1% noise: windows of 31 x 31 cells whose
+    spread is small next to the lane's range."""
+    rng = np.random.default_rng(19)
+    yy, xx = np.mgrid[0:260, 0:640].astype(np.float32)
+    field = np.exp(2.0 * np.sin(xx / 97.0) * np.cos(yy / 61.0)).astype(np.float32)
+    x = (field * (1 + 0.01 * rng.standard_normal(field.shape))).astype(np.float32)
+    y = (0.5 * field + 0.02 * rng.standard_normal(field.shape)).astype(np.float32)
+    for k in (7, 31):
+        c, _ = run(sw, x, y, k)
+        check(c, x, y, k)
