@@ -5,24 +5,14 @@
 
 namespace swc {
 
-constexpr int kTY3 = 8;
-// Output columns of a footprint: as many as keep the TX + K - 1 input columns
-// of the vertical pass within the CTA's 128 threads (one column each, no
-// second round for a few threads), a multiple of 8 so that every footprint's
-// TMA box starts on a 16-byte boundary for both element sizes.
-template <int K>
-constexpr int tx3() {
-  return K3_THREADS - (K - 1 + 7) / 8 * 8;
-}
-
 template <int K>
 static cudaError_t launch_k(const K3DParams& p, int grid, size_t smem, cudaStream_t st) {
   static std::atomic<uint64_t> attr_done{0};  // one bit per device
   cudaError_t e = once_per_device(attr_done, [] {
-    return cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   if (e != cudaSuccess) return e;
-  k3d_kernel<kTY3, tx3<K>(), K, K><<<grid, K3_THREADS, smem, st>>>(p);
+  k3d_kernel<kTY3, tx3<K>(), K, K, false><<<grid, K3_THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -70,10 +60,10 @@ int k3d_blocks_per_sm(int k, size_t smem) {
   switch (k) {
 #define X(K)                                                                                        \
   case K:                                                                                           \
-    e = cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    e = cudaFuncSetAttribute(k3d_kernel<kTY3, tx3<K>(), K, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              200 * 1024);                                                           \
     if (e == cudaSuccess)                                                                           \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k3d_kernel<kTY3, tx3<K>(), K, K>, K3_THREADS, smem); \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k3d_kernel<kTY3, tx3<K>(), K, K, false>, K3_THREADS, smem); \
     break;
     SWC_K3D_CASES(X)
 #undef X

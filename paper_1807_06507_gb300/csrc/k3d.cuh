@@ -32,11 +32,13 @@
 //  * Step 4 (Eq. 2) exactly in int64 once the plane's window is complete.
 // All sums are modular integers (uint32 / uint64), hence exact.
 //  * float32 certificate (fxmap.cuh), evaluated in step 4 from the two
-//    rsqrt factors of c: z = rho n (1/sqrt(vx) + 1/sqrt(vy)) <= 8.99e-6.  A
-//    step in which some window fails asks the whole CTA (once per item)
-//    whether the item's values convert exactly (rho = 0); if not, the
-//    failing windows are recomputed from their cells (fx_recompute) and
-//    stored over the fixed-point results.
+//    rsqrt factors of c: z = rho n (1/sqrt(vx) + 1/sqrt(vy)) <= 8.99e-6.  An
+//    item in which some window fails asks the whole CTA, after its z-march,
+//    whether its values convert exactly (rho = 0); if not, it is listed for
+//    a second launch of the same kernel in its wide form, which marches the
+//    listed items again with a map of up to 26 bits (64-bit first moments,
+//    Eq. 2 in 128-bit integers) and rewrites their windows; the windows that
+//    still fail are recomputed from their own cells, one warp per window.
 #pragma once
 
 #include <type_traits>
@@ -69,6 +71,10 @@ struct K3DParams {
   int unit_stride;     // sz = sy = sx = 1
   int vec_store;       // output rows 16-byte aligned (unit strides)
   long long* sums;     // optional (uint16): 5 int64 per output in C order, Sx Sy Sxx Syy Sxy
+  // float32: items whose windows the 22-bit item map left uncertified (the
+  // first kernel appends them; the wide kernel re-marches them)
+  int* redo_count;
+  int* redo_items;
 };
 
 constexpr int K3_THREADS = 128;
@@ -87,6 +93,16 @@ struct Geo3D {
   static_assert(BXW <= 256, "box too wide");
   static_assert(TX % 8 == 0 && TX <= 128, "footprint width must be a multiple of 8 of at most 128");
 };
+
+constexpr int kTY3 = 8;  // output rows of a footprint
+// Output columns of a footprint: as many as keep the TX + K - 1 input columns
+// of the vertical pass within the CTA's 128 threads (one column each, no
+// second round for a few threads), a multiple of 8 so that every footprint's
+// TMA box starts on a 16-byte boundary for both element sizes.
+template <int K>
+constexpr int tx3() {
+  return K3_THREADS - (K - 1 + 7) / 8 * 8;
+}
 
 // Item exactness: 0 if some in-volume value of cells [z0, z1] x [y0, y1] x
 // [x0, x1] does not convert exactly under the item's maps (every thread of the
@@ -124,9 +140,9 @@ struct Fix3D {
   long long opz, opy;
 };
 
-// Recompute the window of centre (zc, yc, xc) from its cells (fx_recompute)
-// and store it over the fixed-point result.
-static __device__ __noinline__ void fixup_window_3d(const Fix3D& f, int zc, int yc, int xc, uint32_t* status) {
+// Recompute the window of centre (zc, yc, xc) from its cells, the whole warp
+// together (fx_box_warp), and store it over the earlier result.
+static __device__ __noinline__ void fix_window_warp_3d(const Fix3D& f, int zc, int yc, int xc) {
   FxBox b;
   b.gx = f.gx;
   b.gy = f.gy;
@@ -138,40 +154,46 @@ static __device__ __noinline__ void fixup_window_3d(const Fix3D& f, int zc, int 
   b.y1 = min(yc + f.h2, f.H - 1);
   b.x0 = max(xc - f.w1, 0);
   b.x1 = min(xc + f.w2, f.W - 1);
-  f.out[(long long)(zc / f.sz) * f.opz + (long long)(yc / f.sy) * f.opy + xc / f.sx] = fx_recompute(b, status);
+  const float c = fx_box_warp(b, nullptr);
+  if ((threadIdx.x & 31) == 0) f.out[(long long)(zc / f.sz) * f.opz + (long long)(yc / f.sy) * f.opy + xc / f.sx] = c;
 }
 
-// The item's failing windows, after its z-march: the CTA learns whether the
-// item's values convert exactly (then every result stands); otherwise each
-// listed window (n <= cap entries: centre plane << 10 | thread << 3 | bit
-// 4a + c) is recomputed, or, if the list overflowed, every output window of
-// the item (planes [zc0, zc1), rows [y0, y0 + ty), columns [x0, x0 + tx)).
-static __device__ __noinline__ void fixup_item_3d(Fix3D f, const uint64_t* list, int n, int cap, int y0, int x0,
-                                                  int zc0, int zc1, int ty, int tx, int z0, int z1, int ry0,
-                                                  int ry1, int rx0, int rx1, FxMap qx, FxMap qy, uint32_t* status) {
-  if (item_exact_3d(f.gx, f.gy, f.pz, f.py, z0, z1, ry0, ry1, rx0, rx1, qx, qy)) return;
+// The windows the wide re-march of an item could not certify (every thread
+// of the CTA calls it): each listed window (n <= cap entries: centre plane
+// << 10 | thread << 3 | bit 4a + c), or, if the list overflowed, every output
+// window of the item (planes [zc0, zc1), rows [y0, y0 + ty), columns
+// [x0, x0 + tx)), is recomputed by one warp from its own cells.
+static __device__ __noinline__ void fix_listed_3d(Fix3D f, const uint64_t* list, int n, int cap, int y0, int x0,
+                                                  int zc0, int zc1, int ty, int tx, uint32_t* status) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (n <= cap) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = warp; i < n; i += nw) {
       const uint64_t e = list[i];
       const int zc = (int)(e >> 10), t = (int)(e >> 3) & 127, bit = (int)(e & 7);
-      fixup_window_3d(f, zc, y0 + (t >> 5) * 2 + (bit >> 2), x0 + 4 * (t & 31) + (bit & 3), status);
+      fix_window_warp_3d(f, zc, y0 + (t >> 5) * 2 + (bit >> 2), x0 + 4 * (t & 31) + (bit & 3));
     }
+    if (threadIdx.x == 0) atomicAdd(status + ST_FALLBACK, (uint32_t)n);
     return;
   }
   const long long total = (long long)(zc1 - zc0) * ty * tx;
-  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+  for (long long i = warp; i < total; i += nw) {
     const int xc = x0 + (int)(i % tx), yc = y0 + (int)((i / tx) % ty), zc = zc0 + (int)(i / ((long long)tx * ty));
-    if (xc < f.W && yc < f.H && zc % f.sz == 0 && yc % f.sy == 0 && xc % f.sx == 0)
-      fixup_window_3d(f, zc, yc, xc, status);
+    if (xc < f.W && yc < f.H && zc % f.sz == 0 && yc % f.sy == 0 && xc % f.sx == 0) fix_window_warp_3d(f, zc, yc, xc);
   }
 }
 
 #ifndef SWC_K3D_MINB
 #define SWC_K3D_MINB 3  // resident CTAs per SM the 3-D kernel is compiled for
 #endif
-template <int TY, int TX, int KY, int KX>
+// WIDE = false: the kernel for every item (uint16, or float32 with the 22-bit
+// item map).  WIDE = true (float32 only): the second tier, run on the items
+// the first kernel listed, with a finer map of the item's range, fx_wide
+// (up to 26 bits; rho = 1/2), 64-bit first-moment sums and Eq. 2 in 128-bit
+// integers; windows that still fail are recomputed from their own cells.
+template <int TY, int TX, int KY, int KX, bool WIDE>
 __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __grid_constant__ K3DParams p) {
   using G = Geo3D<TY, TX, KY, KX>;
+  using T1 = std::conditional_t<WIDE, uint64_t, uint32_t>;  // first-moment sums
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int esz = p.is_f32 ? 4 : 2;
   const size_t plane_bytes = (size_t)G::TYI * G::BXW * esz;   // one channel of one plane
@@ -189,6 +211,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
   // the float32 maps, the value G of an off-volume cell, the certificate's
   // rounding bounds (0 once the item converts exactly; uint16 is exact)
   __shared__ FxMap sh_qx, sh_qy;
+  __shared__ FxWide sh_wx, sh_wy;
   __shared__ float sh_rho[2];
   // windows whose certificate failed during the item's z-march
   constexpr int kPendCap = 384;
@@ -207,7 +230,9 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
   __syncthreads();
   uint32_t phase_bits = 0;  // parity of each of the 4 barriers
 
-  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+  const int n_iter = WIDE ? *p.redo_count : p.n_items;
+  for (int it = blockIdx.x; it < n_iter; it += gridDim.x) {
+    const int item = WIDE ? p.redo_items[it] : it;
     int rem = item;
     const int xb = rem % p.nxb; rem /= p.nxb;
     const int yb = rem % p.nyb; rem /= p.nyb;
@@ -304,11 +329,18 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       }
       __syncthreads();
       if (tid == 0) {
-        const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
-        sh_qx = qx;
-        sh_qy = qy;
-        sh_rho[0] = qx.rho;
-        sh_rho[1] = qy.rho;
+        if constexpr (WIDE) {
+          const long long nfull = (long long)p.kz * KY * KX;
+          sh_wx = fx_wide(xlo, xhi, nfull);
+          sh_wy = fx_wide(ylo, yhi, nfull);
+          sh_rho[0] = sh_rho[1] = 0.5f;
+        } else {
+          const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
+          sh_qx = qx;
+          sh_qy = qy;
+          sh_rho[0] = qx.rho;
+          sh_rho[1] = qy.rho;
+        }
       }
     } else if (tid == 0) {
       sh_rho[0] = sh_rho[1] = 0.0f;
@@ -317,7 +349,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
     // before their first reads in step 4)
 
     // ---- the z-march
-    uint32_t V0[2][4], V1[2][4];
+    T1 V0[2][4], V1[2][4];
     uint64_t V2[2][4], V3[2][4], V4[2][4];
 #pragma unroll
     for (int a = 0; a < 2; a++)
@@ -372,7 +404,17 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
           const bool row_ok = Y_IN || (gy >= 0 && gy < p.H);
           const int idx = r * G::BXW + G::COFF + c;
           int Xe, Xl, Ye, Yl;
-          if (p.is_f32) {
+          if constexpr (WIDE) {
+            // X = round(x s) - M through a 64-bit conversion (x s is exact);
+            // off-volume cells are absent (X = 0)
+            const float* pe = reinterpret_cast<const float*>(se);
+            const float* pl = reinterpret_cast<const float*>(sl);
+            const bool ie = ue && row_ok, il = ul && row_ok;
+            Xe = ie ? (int)(__float2ll_rn(pe[idx] * sh_wx.s) - sh_wx.M) : 0;
+            Ye = ie ? (int)(__float2ll_rn(pe[yoff + idx] * sh_wy.s) - sh_wy.M) : 0;
+            Xl = il ? (int)(__float2ll_rn(pl[idx] * sh_wx.s) - sh_wx.M) : 0;
+            Yl = il ? (int)(__float2ll_rn(pl[yoff + idx] * sh_wy.s) - sh_wy.M) : 0;
+          } else if (p.is_f32) {
             const float* pe = reinterpret_cast<const float*>(se);
             const float* pl = reinterpret_cast<const float*>(sl);
             const float xl = has_leave ? pl[idx] : 0.f, yl = has_leave ? pl[yoff + idx] : 0.f;
@@ -441,16 +483,17 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       for (int a = 0; a < 2; a++) {
         if (!lane_on) break;
         const int y = warp * 2 + a;
-        uint32_t Q0 = 0u, Q1 = 0u;
+        T1 Q0 = 0u, Q1 = 0u;
         uint64_t Q2 = 0ull, Q3 = 0ull, Q4 = 0ull;
-        uint32_t R0[4], R1[4];
+        T1 R0[4], R1[4];
         uint64_t R2[4], R3[4], R4[4];
         const int plane = TY * G::VSP;
 #pragma unroll
         for (int e = 0; e < 4 + KX - 1; e++) {
           const int cidx = y * G::VSP + 4 * lane + e;
-          Q0 += VS[0 * plane + cidx];
-          Q1 += VS[1 * plane + cidx];
+          // (wide: the ky-row sums of X fit int32; their kx-column sums may not)
+          Q0 += WIDE ? (T1)(long long)(int)VS[0 * plane + cidx] : (T1)VS[0 * plane + cidx];
+          Q1 += WIDE ? (T1)(long long)(int)VS[1 * plane + cidx] : (T1)VS[1 * plane + cidx];
           Q2 += (uint64_t)VS[2 * plane + cidx] | ((uint64_t)VS[3 * plane + cidx] << 32);
           Q3 += (uint64_t)VS[4 * plane + cidx] | ((uint64_t)VS[5 * plane + cidx] << 32);
           Q4 += (uint64_t)VS[6 * plane + cidx] | ((uint64_t)VS[7 * plane + cidx] << 32);
@@ -459,8 +502,8 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
           }
           if (e >= KX - 1) {
             const int c = e - (KX - 1);
-            V0[a][c] += Q0 - (c >= 1 ? R0[c] : 0u);
-            V1[a][c] += Q1 - (c >= 1 ? R1[c] : 0u);
+            V0[a][c] += Q0 - (c >= 1 ? R0[c] : (T1)0u);
+            V1[a][c] += Q1 - (c >= 1 ? R1[c] : (T1)0u);
             V2[a][c] += Q2 - (c >= 1 ? R2[c] : 0ull);
             V3[a][c] += Q3 - (c >= 1 ? R3[c] : 0ull);
             V4[a][c] += Q4 - (c >= 1 ? R4[c] : 0ull);
@@ -477,6 +520,17 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       const float Kx = k0 * rhox * rhox, Ky = k0 * rhoy * rhoy;
       const bool f32 = p.is_f32 != 0;
       auto eval = [&](int a, int c, int cz, uint32_t n32, bool& fail) -> float {
+        if constexpr (WIDE) {
+          // sums of X^2 below 2^62 (fx_wide), first moments 64-bit: Eq. 2 in
+          // 128-bit integers
+          const __int128 n = n32;
+          const long long s0 = (long long)V0[a][c], s1 = (long long)V1[a][c];
+          const __int128 vx = n * (long long)V2[a][c] - (__int128)s0 * s0;
+          const __int128 vy = n * (long long)V3[a][c] - (__int128)s1 * s1;
+          const __int128 num = n * (long long)V4[a][c] - (__int128)s0 * s1;
+          fail = !fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n32, 0.5f, 0.5f);
+          return fx_pearson128(num, vx, vy);
+        }
         // exact in 64-bit modular arithmetic; the results are below 2^63
         const uint64_t n = n32;
         const uint64_t nq2 = n * V2[a][c], nq3 = n * V3[a][c];
@@ -499,7 +553,7 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       };
       // debug output of uint16 plans: the exact window sums of output (jz, jy, jx)
       auto emit = [&](int a, int c, int jz, int jy, int jx) {
-        if (p.sums != nullptr) {
+        if (!WIDE && p.sums != nullptr) {
           long long* s5 = p.sums + 5 * (((long long)jz * p.OY + jy) * p.OX + jx);
           s5[0] = (int)V0[a][c];  // below 2^31 for uint16 windows of at most 32768 cells
           s5[1] = (int)V1[a][c];
@@ -573,12 +627,28 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       __syncthreads();  // VS and the ring slots are reused next step
     }
     // the item's failing windows (float32 only), once its z-march is done
-    if (p.is_f32 && sh_npend > 0) {
-      const Fix3D fx{(const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, p.Z, p.H, p.W, p.hz1, p.hz2,
-                     G::H1, G::H2, G::W1, G::W2, p.sz, p.sy, p.sx, p.out, p.opz, p.opy};
-      fixup_item_3d(fx, sh_pend, sh_npend, kPendCap, y0, x0, zc0, zc1, TY, TX, max(ze0, 0),
-                    min(ze0 + nsteps, p.Z) - 1, max(by, 0), min(by + G::TYI, p.H) - 1, max(x0 - G::W1, 0),
-                    min(x0 - G::W1 + G::TXI, p.W) - 1, sh_qx, sh_qy, p.status);
+    if constexpr (WIDE) {
+      // every window of the item was rewritten; the listed ones are recomputed
+      if (tid == 0) {
+        auto multiples = [](int a, int b, int st) { return (b + st - 1) / st - (a + st - 1) / st; };  // in [a, b)
+        const long long outs = (long long)multiples(zc0, zc1, p.sz) * multiples(y0, min(y0 + TY, p.H), p.sy) *
+                               multiples(x0, min(x0 + TX, p.W), p.sx);
+        atomicAdd(p.status + ST_FALLBACK, (uint32_t)outs);
+      }
+      if (sh_npend > 0) {
+        const Fix3D fx{(const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, p.Z, p.H, p.W, p.hz1, p.hz2,
+                       G::H1, G::H2, G::W1, G::W2, p.sz, p.sy, p.sx, p.out, p.opz, p.opy};
+        fix_listed_3d(fx, sh_pend, sh_npend, kPendCap, y0, x0, zc0, zc1, TY, TX, p.status);
+      }
+      __syncthreads();  // the list and the item constants are reset by the next item
+    } else if (p.is_f32 && sh_npend > 0) {
+      // unless the item's values convert exactly (then every result stands),
+      // list the item for the wide kernel
+      if (!item_exact_3d((const float*)p.gx, (const float*)p.gy, p.ipz, p.ipy, max(ze0, 0),
+                         min(ze0 + nsteps, p.Z) - 1, max(by, 0), min(by + G::TYI, p.H) - 1, max(x0 - G::W1, 0),
+                         min(x0 - G::W1 + G::TXI, p.W) - 1, sh_qx, sh_qy) &&
+          tid == 0)
+        p.redo_items[atomicAdd(p.redo_count, 1)] = item;
       __syncthreads();  // the list and the item constants are reset by the next item
     }
   }

@@ -50,6 +50,8 @@ struct Geo3DInfo {
 struct K3DParams;
 bool k3d_geometry(int k, Geo3DInfo* g);
 cudaError_t k3d_launch(int k, const K3DParams& p, int grid, size_t smem, cudaStream_t st);
+// float32 second tier: the wide kernel over the items the first launch listed
+cudaError_t k3d_wide_launch(int k, const K3DParams& p, int grid, size_t smem, cudaStream_t st);
 // resident CTAs per SM of that instance with `smem` bytes (0 if the query fails)
 int k3d_blocks_per_sm(int k, size_t smem);
 

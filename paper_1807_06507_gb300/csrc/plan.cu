@@ -309,6 +309,8 @@ struct swcorr_plan_s {
   int64_t cached_pitch = -1;
   // device status block
   uint32_t* d_status = nullptr;
+  // float32 3-D plans: count and list of the items left to the wide kernel
+  int* d_redo = nullptr;
   // batched plans: device block (scenes, tensor maps, items, counter), graph
   void* d_batch = nullptr;
   KBatchParams kbs[3]{};  // launches per kernel class (32-bit; 64-bit <= 17 columns; 64-bit wider)
@@ -534,8 +536,19 @@ static swcorr_status run_3d(swcorr_plan_s* p, const void* x, const void* y, cons
   k3.unit_stride = (k3.sz == 1 && k3.sy == 1 && k3.sx == 1) ? 1 : 0;
   k3.vec_store = (k3.unit_stride && (reinterpret_cast<uintptr_t>(c) & 15) == 0 && k3.opy % 4 == 0 && k3.opz % 4 == 0)
                      ? 1 : 0;
-  cudaError_t e = k3d_launch(p->k[2], k3, p->grid, p->smem, st);
+  cudaError_t e;
+  if (k3.is_f32) {
+    // items the 22-bit map leaves uncertified go to the wide kernel
+    k3.redo_count = p->d_redo;
+    k3.redo_items = p->d_redo + 1;
+    if ((e = cudaMemsetAsync(p->d_redo, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "3-D item list reset");
+  } else {
+    k3.redo_count = k3.redo_items = nullptr;
+  }
+  e = k3d_launch(p->k[2], k3, p->grid, p->smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "3-D kernel launch");
+  if (k3.is_f32 && (e = k3d_wide_launch(p->k[2], k3, p->grid, p->smem, st)) != cudaSuccess)
+    return cuda_fail(e, "3-D wide kernel launch");
   return SWCORR_OK;
 }
 
@@ -735,6 +748,14 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     return cuda_fail(e, "cudaMemset(status)");
   }
   p->k2.status = p->d_status;
+  if (p->kind == KIND_3D && p->dtype == SWCORR_F32) {
+    e = cudaMalloc(&p->d_redo, ((size_t)p->k3.n_items + 1) * sizeof(int));
+    if (e != cudaSuccess) {
+      swcorr_plan_destroy(p);
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "3-D item list: out of device memory")
+                                            : cuda_fail(e, "cudaMalloc(3-D item list)");
+    }
+  }
   if (p->kind == KIND_ND) {
     // two stream buffers, scratch, and for the cumulative-sum ablation the
     // segment totals of the widest pass (at most ncell / 128 + lines per stream)
@@ -1073,6 +1094,7 @@ void swcorr_plan_destroy(swcorr_plan p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->d_batch);
   cudaFree(p->d_nd);
+  cudaFree(p->d_redo);
   cudaFree(p->d_status);
   cudaFree(p->d_x);
   cudaFree(p->d_y);
