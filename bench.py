@@ -228,6 +228,25 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
                                       **_scored_dc(sets[0][2].cpu().numpy(), xf, yf, K, None, idx)}
     del sets, p
 
+    # float32 data off the integers: the night scene's visible channel scaled
+    # by 0.37 (lights thousands of times the dark level), and a smooth
+    # radiance-like field with 1% noise; many lanes take the second tier
+    for name, (xa, ya) in (("scaled_night_f32_3000x4000_k7", (vis.astype(np.float32) * np.float32(0.37), yf)),
+                           ("smooth_field_f32_3000x4000_k7", workloads.smooth_field_pair(vis.shape))):
+        p = swcorr.Plan(xa.shape, K, dtype="f32")
+        sets = [(to(xa), to(ya), torch.empty(xa.shape, dtype=torch.float32, device=dev)) for _ in range(3)]
+        p.fallbacks()
+        t = _events_time(torch, lambda i: p.run(*sets[i % 3][:2], c=sets[i % 3][2]), 10)
+        p.check_status()
+        fb = p.fallbacks() / 12.0
+        idx = rng.integers(0, xa.size, 50_000)
+        out[name] = {"windows_per_s": xa.size / t, "us_per_launch": t * 1e6,
+                     "rewritten_windows_per_launch": fb,
+                     "gbs_algorithmic": xa.size * BYTES_PER_WINDOW_F32 / t / 1e9,
+                     **_scored_dc(sets[0][2].cpu().numpy(), xa, ya, K, None, idx)}
+        del sets, p
+    del xf, yf
+
     # 1-D random walk, 2^26 samples, window 1001
     x1, y1 = workloads.random_walk_pair(1 << 26)
     p = swcorr.Plan(x1.shape, 1001, dtype="f32")
@@ -262,6 +281,22 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
             **_scored_dc(c3.cpu().numpy(), x3, y3, 9, st, idx)}
         del c3, p
     del xd, yd, x3, y3
+    # a smooth radiance-like volume with 1% noise (most items take the wide
+    # second tier)
+    x3, y3 = workloads.smooth_field_pair((128, 256, 512))
+    xd, yd = to(x3), to(y3)
+    p = swcorr.Plan(x3.shape, 9, dtype="f32")
+    c3 = torch.empty(p.oshape, dtype=torch.float32, device=dev)
+    p.fallbacks()
+    t = _events_time(torch, lambda i: p.run(xd, yd, c=c3), 10)
+    p.check_status()
+    fb = p.fallbacks() / 12.0
+    idx = rng.integers(0, c3.numel(), 50_000)
+    out["smooth_field_3d_128x256x512_k9"] = {
+        "windows_per_s": c3.numel() / t, "us_per_launch": t * 1e6,
+        "gbs_algorithmic": c3.numel() * BYTES_PER_WINDOW_F32 / t / 1e9, "rewritten_windows_per_launch": fb,
+        **_scored_dc(c3.cpu().numpy(), x3, y3, 9, None, idx)}
+    del c3, p, xd, yd, x3, y3
 
     # general n-D path (the paper's scheme of one sum pass per dimension over
     # materialised streams): a 4-D float32 grid, the paper's -2 convention on
@@ -304,17 +339,21 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
     p.close()
     del sets
 
-    # 64 uneven scenes: one batched launch vs 64 plain launches, uint16 and
-    # float32 (the uint16 scenes scaled by 0.37: values off the integers)
+    # 64 uneven scenes: one batched launch vs 64 plain launches, uint16, the
+    # same scenes as float32, and float32 with the visible channel scaled by
+    # 0.37 (values off the integers: many lanes take the second tier)
     scenes = workloads.batched_scenes(64)
     nwin = sum(sc.x.size for sc in scenes)
-    for dt in ("u16", "f32"):
+    for variant in ("u16", "f32", "f32_scaled"):
+        dt = variant[:3]
         dv, hosts = [], []
         for sc in scenes:
             h, w = sc.x.shape
             wp = -(-w // 8) * 8
             if dt == "u16":
                 hx, hy = sc.x, sc.y
+            elif variant == "f32":
+                hx, hy = sc.x.astype(np.float32), sc.y.astype(np.float32)
             else:
                 hx, hy = sc.x.astype(np.float32) * np.float32(0.37), sc.y.astype(np.float32)
             xp = np.zeros((h, wp), hx.dtype)
@@ -343,7 +382,7 @@ def secondary(torch, swcorr, workloads, dev, vis, ir):
             ii = rng.integers(0, sc.x.size, 2000)
             dcs.append(_scored_dc(g, hx, hy, sc.k, None, ii)["max_abs_dc_sampled"])
         bpw = BYTES_PER_WINDOW_U16 if dt == "u16" else BYTES_PER_WINDOW_F32
-        out[f"batched_64_scenes_{dt}"] = {
+        out[f"batched_64_scenes_{variant}"] = {
             "windows": nwin, "batched_windows_per_s": nwin / tb, "plain_windows_per_s": nwin / tp,
             "batched_ms": tb * 1e3, "plain_ms": tp * 1e3, "speedup": tp / tb,
             "gbs_algorithmic_batched": nwin * bpw / tb / 1e9, "recomputed_windows_per_launch": fb / 12.0,

@@ -5,9 +5,10 @@
 // row block) sit in a device array ordered largest cost first; each CTA (one
 // warp) takes the next item from an atomic counter and runs the fused 2-D
 // float32 body (k2d_f32.cuh: per-lane fixed-point map, exact integer sums,
-// per-window certificate, recomputation of failing windows) specialised for
-// that scene's window width.  The plan replays one CUDA graph: a memset node
-// resetting the counter, then this kernel.
+// per-window certificate, second-tier re-march of the lanes it leaves
+// uncertified).  Scenes are grouped by window width, one kernel instance per
+// width; the plan replays one CUDA graph: a memset node resetting the
+// counters, then one launch per width that has scenes.
 #include "k2d_f32.cuh"
 #include "launch.h"
 
@@ -18,10 +19,9 @@ namespace {
 constexpr int kRWS = Geo2DF<8, 31>::RWS;  // the same for every instance with M = 8
 static_assert(Geo2DF<8, 1>::RWS == kRWS && Geo2DF<8, 17>::RWS == kRWS, "ring rows differ between instances");
 
-// One instance per class of window width (0: up to 9 columns, 1: up to 17,
-// 2: up to 31), so that each instance holds the registers of its own bodies
-// only.
-template <int CLS>
+// One instance per window width (class (KW - 1) / 2), so that each kernel
+// holds the registers of its own body only.
+template <int KW>
 __global__ void __launch_bounds__(32, 12) kbatched_f32_kernel(const __grid_constant__ KBatchParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring2DF rg;
@@ -51,17 +51,11 @@ __global__ void __launch_bounds__(32, 12) kbatched_f32_kernel(const __grid_const
     const BatchItem it = p.items[item];
     const Scene2D sc = p.scenes[it.scene];
     bool ok = true;
-    switch (sc.kw) {
-#define X(KW, C)                                                                                     \
-  case KW:                                                                                           \
-    if constexpr (CLS == C) ok = process_item_2d_f32<8, KW, true>(sc, it.strip, it.rb, rg, seq, p.status); \
-    break;
-      X(1, 0) X(3, 0) X(5, 0) X(7, 0) X(9, 0) X(11, 1) X(13, 1) X(15, 1) X(17, 1)
-      X(19, 2) X(21, 2) X(23, 2) X(25, 2) X(27, 2) X(29, 2) X(31, 2)
-#undef X
-      default:
-        if (lane == 0) atomicOr(p.status + ST_ERROR, ERRBIT_BAD_ARG);
-        ok = false;
+    if (sc.kw == KW) {
+      ok = process_item_2d_f32<8, KW, true>(sc, it.strip, it.rb, rg, seq, p.status);
+    } else {
+      if (lane == 0) atomicOr(p.status + ST_ERROR, ERRBIT_BAD_ARG);
+      ok = false;
     }
     if (!ok) return;
   }
@@ -71,26 +65,38 @@ __global__ void __launch_bounds__(32, 12) kbatched_f32_kernel(const __grid_const
 
 int kbatched_f32_ring_row() { return kRWS; }
 
+#define SWC_KB32_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31)
+
 const void* kbatched_f32_kernel_ptr(int cls) {
-  return cls == 0 ? reinterpret_cast<const void*>(kbatched_f32_kernel<0>)
-                  : cls == 1 ? reinterpret_cast<const void*>(kbatched_f32_kernel<1>)
-                             : reinterpret_cast<const void*>(kbatched_f32_kernel<2>);
+  switch (2 * cls + 1) {
+#define X(KW) \
+  case KW:    \
+    return reinterpret_cast<const void*>(kbatched_f32_kernel<KW>);
+    SWC_KB32_CASES(X)
+#undef X
+    default:
+      return nullptr;
+  }
 }
 
 cudaError_t kbatched_f32_prepare() {
   cudaError_t e = cudaSuccess;
-  for (int c = 0; c < 3 && e == cudaSuccess; c++)
+  for (int c = 0; c < 16 && e == cudaSuccess; c++)
     e = cudaFuncSetAttribute(kbatched_f32_kernel_ptr(c), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return e;
 }
 
 cudaError_t kbatched_f32_launch(const KBatchParams& p, int cls, int grid, size_t smem, cudaStream_t st) {
-  if (cls == 0)
-    kbatched_f32_kernel<0><<<grid, 32, smem, st>>>(p);
-  else if (cls == 1)
-    kbatched_f32_kernel<1><<<grid, 32, smem, st>>>(p);
-  else
-    kbatched_f32_kernel<2><<<grid, 32, smem, st>>>(p);
+  switch (2 * cls + 1) {
+#define X(KW)                                              \
+  case KW:                                                 \
+    kbatched_f32_kernel<KW><<<grid, 32, smem, st>>>(p);    \
+    break;
+    SWC_KB32_CASES(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

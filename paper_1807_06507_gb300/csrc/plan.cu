@@ -274,6 +274,8 @@ swcorr_status bind_2d_u16(K2DParams* k2, const Geo2DInfo& g2, const void* x, con
 
 }  // namespace swc
 
+constexpr int kMaxBatchClasses = 16;
+
 enum PlanKind { KIND_2D_U16 = 1, KIND_2D_F32 = 2, KIND_1D = 3, KIND_3D = 4, KIND_ND = 5, KIND_BATCHED = 10 };
 
 struct swcorr_plan_s {
@@ -313,8 +315,11 @@ struct swcorr_plan_s {
   int* d_redo = nullptr;
   // batched plans: device block (scenes, tensor maps, items, counter), graph
   void* d_batch = nullptr;
-  KBatchParams kbs[3]{};  // launches per kernel class (32-bit; 64-bit <= 17 columns; 64-bit wider)
-  int bgrid[3] = {0, 0, 0};
+  // launches per kernel class: uint16 3 (32-bit engine; 64-bit up to 17
+  // columns; 64-bit wider), float32 16 (one per window width)
+  KBatchParams kbs[kMaxBatchClasses]{};
+  int bgrid[kMaxBatchClasses] = {};
+  int n_cls = 0;
   int64_t batched_outputs = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -1139,7 +1144,9 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   } else if (!tune_lookup(dev.name, "batched", 2, nullptr, dtype, &tn)) {
     tn = swcorr_tune{};
   }
-  const int rows_min = tn.tile_rows > 0 ? tn.tile_rows : 64;
+  // least output rows per work item (float32: taller items amortise the
+  // second tier's halo rows; 128 measured best on mixed scenes)
+  const int rows_min = tn.tile_rows > 0 ? tn.tile_rows : (f32 ? 128 : 64);
   cudaError_t e = f32 ? kbatched_f32_prepare() : kbatched_prepare();
   if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
 
@@ -1206,13 +1213,16 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   // items grouped by kernel class (32-bit engine; 64-bit up to 17 columns;
   // 64-bit above), one launch each
+  // (float32: one class per window width, so that each kernel holds the
+  // registers of its own body only)
+  const int n_cls = f32 ? kMaxBatchClasses : 3;
   auto cls_of = [&](int i) {
-    if (f32) return sc[i].kw <= 9 ? 0 : (sc[i].kw <= 17 ? 1 : 2);
+    if (f32) return (sc[i].kw - 1) / 2;
     return sc[i].wide == 0 ? 0 : (sc[i].kw <= 17 ? 1 : 2);
   };
   std::vector<BatchItem> items;
-  size_t cls_start[4] = {0, 0, 0, 0};
-  for (int cls = 0; cls < 3; cls++) {
+  size_t cls_start[kMaxBatchClasses + 1] = {};
+  for (int cls = 0; cls < n_cls; cls++) {
     cls_start[cls] = items.size();
     for (int i : order) {
       if (cls_of(i) != cls) continue;
@@ -1220,7 +1230,7 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
         for (int strip = 0; strip < sc[i].n_strips; strip++) items.push_back(BatchItem{i, strip, rb, 0});
     }
   }
-  cls_start[3] = items.size();
+  cls_start[n_cls] = items.size();
   if (items.size() > (size_t)0x7fffffff) return fail(SWCORR_ERR_UNSUPPORTED, "too many work items");
 
   // one device block: maps (64-byte aligned), scenes, items, counter
@@ -1236,6 +1246,7 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
   p->dtype = dtype;
   p->dev = dev;
   p->batched_outputs = outputs;
+  p->n_cls = n_cls;
   auto cleanup = [&](swcorr_status s) {
     swcorr_plan_destroy(p);
     return s;
@@ -1259,11 +1270,11 @@ swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* sc
       (e = cudaMemset(base + ctr_off, 0, 256)) != cudaSuccess ||
       (e = cudaMemset(p->d_status, 0, ST_WORDS * sizeof(uint32_t))) != cudaSuccess)
     return cleanup(cuda_fail(e, "batched plan upload"));
-  const int PF = tn.prefetch > 0 ? tn.prefetch : 4;
+  const int PF = tn.prefetch > 0 ? tn.prefetch : (f32 ? 3 : 4);  // (float32: as the plain kernel)
   p->smem = f32 ? (size_t)4 * (PF + 1) * kbatched_f32_ring_row() * 4 + (size_t)(PF + 1) * 8
                 : (size_t)4 * (PF + 1) * kbatched_ring_row() * 2 + (size_t)(PF + 1) * 8;
   int per_sm_max = 0;
-  for (int cls = 0; cls < 3; cls++) {
+  for (int cls = 0; cls < n_cls; cls++) {
     KBatchParams& kb = p->kbs[cls];
     kb.scenes = reinterpret_cast<const Scene2D*>(base + sc_off);
     kb.items = reinterpret_cast<const BatchItem*>(base + it_off) + cls_start[cls];
@@ -1299,9 +1310,11 @@ swcorr_status swcorr_run_batched(swcorr_plan p, void* stream) {
       return cuda_fail(e, "create capture stream");
     if ((e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, 3 * sizeof(uint32_t), p->cap_stream);
-    cudaError_t e2 = cudaSuccess;
-    for (int cls = 0; cls < 3 && e2 == cudaSuccess; cls++)
+    cudaError_t e1 = cudaMemsetAsync(p->kbs[0].counter, 0, (size_t)p->n_cls * sizeof(uint32_t), p->cap_stream);
+    // one launch per class with items, in sequence (concurrent branches let
+    // the classes' CTAs share the SMs, which measured slower)
+    cudaError_t e2 = e1;
+    for (int cls = 0; cls < p->n_cls && e2 == cudaSuccess; cls++)
       if (p->kbs[cls].n_items > 0)
         e2 = p->dtype == SWCORR_F32 ? kbatched_f32_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream)
                                     : kbatched_launch(p->kbs[cls], cls, p->bgrid[cls], p->smem, p->cap_stream);

@@ -213,6 +213,26 @@ def batched_scenes(n_scenes=64, seed=seed_for(5), w_range=(1024, 6000), h_range=
     return scenes
 
 
+# ---------------------------------------------------- float data off the grid
+def smooth_field_pair(shape, seed=seed_for(7), noise=0.01):
+    """A smooth log-normal field f = exp(2 prod_d trig(i_d / L_d)) on a grid of
+    any dimension (L = 97, 61, 43, ... cells; sin on the last axis, cos on
+    the others), x = f (1 + noise N(0,1)), y = f / 2 + 2 noise N(0,1)
+    (float32): radiance-like data whose windows have a spread small next to
+    the range of the tile they sit in."""
+    rng = np.random.default_rng(seed)
+    scales = (97.0, 61.0, 43.0, 37.0, 29.0, 23.0, 19.0, 17.0)
+    arg = np.ones(shape, dtype=np.float64)
+    for d, n in enumerate(shape):
+        ax = np.arange(n, dtype=np.float64) / scales[len(shape) - 1 - d]
+        trig = np.sin(ax) if d == len(shape) - 1 else np.cos(ax)
+        arg = arg * trig.reshape((1,) * d + (n,) + (1,) * (len(shape) - 1 - d))
+    f = np.exp(2.0 * arg).astype(np.float32)
+    x = (f * (1 + noise * rng.standard_normal(shape))).astype(np.float32)
+    y = (0.5 * f + 2 * noise * rng.standard_normal(shape)).astype(np.float32)
+    return x, y
+
+
 # ------------------------------------------------------- n-dimensional grids
 def correlated_grid_pair(shape, seed=seed_for(6), rho=0.5):
     """x ~ N(0,1) iid on a grid of any dimension; y = rho x + N(0,1) noise

@@ -172,3 +172,22 @@ def test_2d_smooth_radiance_field(sw):
     for k in (7, 31):
         c, _ = run(sw, x, y, k)
         check(c, x, y, k)
+
+
+@pytest.mark.parametrize("k,stride", [(9, 1), (5, 2)])
+def test_3d_smooth_field_and_sparse_spots(sw, k, stride):
+    """A smooth log-normal volume with 1% noise, and N(0, 1) data with sparse
+    spots of 1e3: most items need the wide second tier."""
+    rng = np.random.default_rng(23 + k)
+    shape = (20, 44, 150)
+    zz, yy, xx = np.meshgrid(*(np.arange(n, dtype=np.float32) for n in shape), indexing="ij")
+    field = np.exp(2.0 * np.sin(xx / 37.0) * np.cos(yy / 23.0) * np.cos(zz / 17.0)).astype(np.float32)
+    fx = (field * (1 + 0.01 * rng.standard_normal(shape))).astype(np.float32)
+    fy = (0.5 * field + 0.02 * rng.standard_normal(shape)).astype(np.float32)
+    sx = rng.standard_normal(shape).astype(np.float32)
+    sy = (0.5 * sx + rng.standard_normal(shape)).astype(np.float32)
+    sx.reshape(-1)[rng.integers(0, sx.size, sx.size // 5000)] = np.float32(1e3)
+    for x, y in ((fx, fy), (sx, sy)):
+        c, fb = run(sw, x, y, k, stride)
+        check(c, x, y, k, stride)
+        assert fb > 0
