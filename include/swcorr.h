@@ -122,8 +122,8 @@ enum {
 typedef struct swcorr_plan_s* swcorr_plan;
 
 /* Create a plan for one problem shape (the windowed correlation of two
- * equal-size grids, Section 3: "both sets of data must be the same size";
- * window size and step, Introduction).
+ * equal-size grids, Section 3: both data sets have the same size; window
+ * size and step, Introduction).
  *   out    : receives the plan (set to NULL on failure).
  *   ndim   : 1 to 8.  1-D, 2-D and 3-D grids with clipped windows run one
  *            fused kernel (Section 1, steps 1-4 in one pass over HBM); more
@@ -132,10 +132,12 @@ typedef struct swcorr_plan_s* swcorr_plan;
  *            sums, one per dimension: Section 1's n-dimensional
  *            generalisation, Section 2's parallel phases).
  *   shape  : ndim extents, each >= 1 and at most 2^31 - 1024.
- *   k      : ndim window sizes, each >= 1.  The fused 2-D and 3-D kernels take
- *            windows up to 31 in the contiguous dimension (odd), the 3-D one
- *            with equal row and column sizes up to 15; uint16 windows hold at
- *            most 32768 in-bounds cells.  SWCORR_ERR_UNSUPPORTED otherwise.
+ *   k      : ndim window sizes, each >= 1 (an even k gives the window
+ *            [i - k/2 + 1, i + k/2]).  The fused 2-D kernel takes odd widths
+ *            up to 31 in the contiguous dimension, the fused 3-D one equal
+ *            odd row and column sizes up to 15; uint16 windows of the fused
+ *            kernels hold at most 32768 in-bounds cells.  Any other window
+ *            shape runs on the general path (same results).
  *   stride : ndim steps >= 1, or NULL for all ones (Introduction: "given
  *            step").
  *   dtype  : SWCORR_U16 or SWCORR_F32 (x and y share it).
@@ -150,7 +152,7 @@ swcorr_status swcorr_plan_create(swcorr_plan* out, int ndim, const int64_t* shap
                                  swcorr_border border, uint32_t flags);
 
 /* Launch parameters of a plan, as chosen by the autotuner (support
- * component; the paper has no counterpart).  0 in a field = the library's
+ * component; no counterpart in the paper).  0 in a field = the library's
  * built-in default.
  *   prefetch    : rows (2-D) in flight ahead of the row being summed: the
  *                 depth of the shared-memory staging ring (1..8).
@@ -177,12 +179,13 @@ typedef struct {
 /* swcorr_plan_create with explicit launch parameters (tune != NULL) instead
  * of the tune cache's entry for this device, ndim, dtype and k.  Values
  * outside the ranges above give SWCORR_ERR_INVALID_ARG.  Used by the
- * autotuner to time candidates. */
+ * autotuner to time candidates.  No counterpart in the paper. */
 swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t* shape,
                                        const int32_t* k, const int32_t* stride, swcorr_dtype dtype,
                                        swcorr_border border, uint32_t flags, const swcorr_tune* tune);
 
-/* The launch parameters a plan uses (after defaults and the cache). */
+/* The launch parameters a plan uses (after defaults and the cache).  No
+ * counterpart in the paper.  SWCORR_ERR_INVALID_ARG for a NULL argument. */
 swcorr_status swcorr_plan_tune(swcorr_plan p, swcorr_tune* out);
 
 /* Tune cache: a JSON file ({"format": "swcorr-tune-1", "entries": [...]},
@@ -192,17 +195,21 @@ swcorr_status swcorr_plan_tune(swcorr_plan p, swcorr_tune* out);
  * SWCORR_TUNE_FILE environment variable, if set.  A file that cannot be read
  * or does not parse is ignored as a whole (SWCORR_ERR_INVALID_ARG here, the
  * built-in defaults apply).  Thread-safe; plans already created keep their
- * parameters. */
+ * parameters.  No counterpart in the paper. */
 swcorr_status swcorr_set_tune_file(const char* path);
 
 /* Cache lookup without a device (tests, tools): 1 and *out filled if the
  * loaded cache has an entry for (device, kind, ndim, k, dtype), else 0.
  * device NULL matches any device; batched != 0 looks up the batched plan's
- * entry (k ignored). */
+ * entry (k ignored).  No counterpart in the paper. */
 int swcorr_tune_lookup(const char* device, int batched, int ndim, const int32_t* k, swcorr_dtype dtype,
                        swcorr_tune* out);
 
-/* Queue the correlation of device buffers x, y into device buffer c.
+/* Queue the correlation of device buffers x, y into device buffer c: for
+ * every output window the five sums of x, y, x^2, y^2 and xy (Section 1,
+ * steps 1-3) and Pearson's c from them (Section 1, Eq. 2: the sums form of
+ * the classical formula of the Introduction), NaN for a window whose x or y
+ * values are all equal (Section 3, accuracy paragraph), clamped to [-1, 1].
  *   x, y      : device pointers, 16-byte aligned, plan dtype.
  *   in_pitch  : ndim element pitches for x and y, or NULL (contiguous); the
  *               byte pitch of every outer dimension must be a multiple of 16.
@@ -211,11 +218,17 @@ int swcorr_tune_lookup(const char* device, int batched, int ndim, const int32_t*
  *   sums      : device int64 buffer of 5 * (number of outputs) entries when the
  *               plan has SWCORR_FLAG_EMIT_SUMS, else NULL.
  *   stream    : cudaStream_t.
- * Returns after queuing (asynchronous). */
+ * Returns after queuing (asynchronous).  Argument errors are returned
+ * synchronously (SWCORR_ERR_INVALID_ARG, SWCORR_ERR_ALIGNMENT); device-side
+ * ones are read with swcorr_plan_status after the stream has synchronised.
+ * The caller owns x, y, c and sums and keeps them alive until the stream
+ * work completes. */
 swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int64_t* in_pitch,
                          float* c, const int64_t* out_pitch, int64_t* sums, void* stream);
 
-/* Same computation from HOST buffers: copies x and y to plan-owned device
+/* Same computation from HOST buffers (the paper's GPU timing in Section 3
+ * includes the copies to and from the device; this call is that whole
+ * job): copies x and y to plan-owned device
  * staging buffers, runs, copies c back and synchronises the stream.  Host
  * buffers are contiguous; pinned memory gives the fastest copies.  The plan
  * allocates its staging buffers on the first call (SWCORR_ERR_OOM on failure).
@@ -259,21 +272,29 @@ swcorr_status swcorr_plan_batched(swcorr_plan* out, const swcorr_scene* scenes, 
                                   swcorr_dtype dtype, uint32_t flags);
 
 /* swcorr_plan_batched with explicit launch parameters (see swcorr_tune;
- * tile_rows is the least number of output rows per work item). */
+ * tile_rows is the least number of output rows per work item).  No
+ * counterpart in the paper. */
 swcorr_status swcorr_plan_batched_tuned(swcorr_plan* out, const swcorr_scene* scenes, int n_scenes,
                                         swcorr_dtype dtype, uint32_t flags, const swcorr_tune* tune);
 
-/* Launch the batched plan on a stream (graph launch). */
+/* Launch the batched plan on a stream (graph launch; asynchronous).  The
+ * paper correlates one scene per run; batching many is this library's
+ * scheduling, with no counterpart in the paper.  SWCORR_ERR_INVALID_ARG
+ * for a plan that is not batched. */
 swcorr_status swcorr_run_batched(swcorr_plan p, void* stream);
 
 /* Device-side status latched by the plan's kernels (read after the stream
- * has synchronised; reading resets it).  SWCORR_OK if nothing went wrong. */
+ * has synchronised; reading resets it).  SWCORR_OK if nothing went wrong,
+ * SWCORR_ERR_TIMEOUT if a bounded wait gave up (that work item's outputs are
+ * undefined).  No counterpart in the paper. */
 swcorr_status swcorr_plan_status(swcorr_plan p);
 
-/* Diagnostic: number of windows the plan's kernels recomputed through the
- * exact per-window path since the last call (uint16: windows whose
- * second-moment sums could not be certified below 2^32; float32: windows
- * whose fixed-point certificate failed); reading resets it.  -1 on error. */
+/* Diagnostic: number of windows the plan's kernels computed again since the
+ * last call (uint16: windows whose second-moment sums could not be
+ * certified below 2^32, recomputed exactly; float32: windows rewritten by
+ * the second tier, which re-marches a lane or item whose fixed-point map
+ * left a window uncertified, plus windows recomputed from their own cells);
+ * reading resets it.  -1 on error.  No counterpart in the paper. */
 int64_t swcorr_plan_fallbacks(swcorr_plan p);
 
 /* No-allocation 2-D uint16 run, for callers that cannot allocate device
@@ -316,19 +337,23 @@ swcorr_status swcorr_run2d_u16_noalloc(int64_t rows, int64_t cols, int32_t kh, i
  * paper has no counterpart. */
 swcorr_status swcorr_noalloc_status(void* stream, int64_t* fallbacks);
 
-/* Number of output windows the plan computes per run. */
+/* Number of output windows the plan computes per run (the product of
+ * ceil(shape[d] / stride[d])).  -1 for NULL. */
 int64_t swcorr_plan_outputs(swcorr_plan p);
 
 /* Release a plan (NULL is ignored).  Waits for nothing: the caller must have
- * synchronised the streams the plan ran on. */
+ * synchronised the streams the plan ran on.  No counterpart in the paper. */
 void swcorr_plan_destroy(swcorr_plan p);
 
+/* Name of a status code (static string).  No counterpart in the paper. */
 const char* swcorr_status_string(swcorr_status s);
 
-/* Detail text of the last failing call on this thread ("" if none). */
+/* Detail text of the last failing call on this thread ("" if none).  No
+ * counterpart in the paper. */
 const char* swcorr_last_error(void);
 
-/* Library version, e.g. "swcorr 0.1.0 sm_103a". */
+/* Library version, e.g. "swcorr 0.1.0 sm_103a".  No counterpart in the
+ * paper. */
 const char* swcorr_version(void);
 
 #ifdef __cplusplus

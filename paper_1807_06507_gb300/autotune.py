@@ -78,6 +78,8 @@ CONFIGS = {
                   dict(tile_rows=[8, 16, 32], ctas_per_sm=[1, 2, 3, 4])),
     "batched_u16": ("batched", "u16", None, None, None,
                     dict(prefetch=[2, 3, 4, 6], tile_rows=[16, 32, 64, 128])),
+    "batched_f32": ("batched", "f32", None, None, None,
+                    dict(prefetch=[2, 3, 4], tile_rows=[64, 96, 128, 192])),
 }
 
 
@@ -146,8 +148,9 @@ def tune_batched(torch, name, reps, log):
     for s in scenes:
         h, w = s.x.shape
         wp = -(-w // 8) * 8
-        xp = np.zeros((h, wp), np.uint16)
-        yp = np.zeros((h, wp), np.uint16)
+        et = np.uint16 if dtype == "u16" else np.float32  # float32: the exact cast
+        xp = np.zeros((h, wp), et)
+        yp = np.zeros((h, wp), et)
         xp[:, :w], yp[:, :w] = s.x, s.y
         dv.append((_dev(torch, xp)[:, :w], _dev(torch, yp)[:, :w],
                    torch.empty((h, w), dtype=torch.float32, device="cuda"), s.k))
