@@ -477,39 +477,56 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
       }
 
       // horizontal pass: warp -> 2 output rows, lane -> 4 output columns
-      // (lanes past the footprint's TX columns have none)
+      // (lanes past the footprint's TX columns have none).  Strided plans
+      // (a variant of their own, so that unit strides pay nothing) skip rows
+      // that are not output rows and update the running sums of output
+      // columns only (col_mask bit c: column xc0 + c is one).
       const bool lane_on = lane < G::LANES;
+      auto hpass = [&](auto strided_tag) {
+        constexpr bool STRIDED = decltype(strided_tag)::value;
+        uint32_t col_mask = 0xFu;
+        if constexpr (STRIDED) {
+          col_mask = 0u;
 #pragma unroll
-      for (int a = 0; a < 2; a++) {
-        if (!lane_on) break;
-        const int y = warp * 2 + a;
-        T1 Q0 = 0u, Q1 = 0u;
-        uint64_t Q2 = 0ull, Q3 = 0ull, Q4 = 0ull;
-        T1 R0[4], R1[4];
-        uint64_t R2[4], R3[4], R4[4];
-        const int plane = TY * G::VSP;
+          for (int c = 0; c < 4; c++) col_mask |= ((x0 + 4 * lane + c) % p.sx == 0) ? (1u << c) : 0u;
+        }
 #pragma unroll
-        for (int e = 0; e < 4 + KX - 1; e++) {
-          const int cidx = y * G::VSP + 4 * lane + e;
-          // (wide: the ky-row sums of X fit int32; their kx-column sums may not)
-          Q0 += WIDE ? (T1)(long long)(int)VS[0 * plane + cidx] : (T1)VS[0 * plane + cidx];
-          Q1 += WIDE ? (T1)(long long)(int)VS[1 * plane + cidx] : (T1)VS[1 * plane + cidx];
-          Q2 += (uint64_t)VS[2 * plane + cidx] | ((uint64_t)VS[3 * plane + cidx] << 32);
-          Q3 += (uint64_t)VS[4 * plane + cidx] | ((uint64_t)VS[5 * plane + cidx] << 32);
-          Q4 += (uint64_t)VS[6 * plane + cidx] | ((uint64_t)VS[7 * plane + cidx] << 32);
-          if (e <= 2) {
-            R0[e + 1] = Q0; R1[e + 1] = Q1; R2[e + 1] = Q2; R3[e + 1] = Q3; R4[e + 1] = Q4;
-          }
-          if (e >= KX - 1) {
-            const int c = e - (KX - 1);
-            V0[a][c] += Q0 - (c >= 1 ? R0[c] : (T1)0u);
-            V1[a][c] += Q1 - (c >= 1 ? R1[c] : (T1)0u);
-            V2[a][c] += Q2 - (c >= 1 ? R2[c] : 0ull);
-            V3[a][c] += Q3 - (c >= 1 ? R3[c] : 0ull);
-            V4[a][c] += Q4 - (c >= 1 ? R4[c] : 0ull);
+        for (int a = 0; a < 2; a++) {
+          if (!lane_on) break;
+          const int y = warp * 2 + a;
+          if (STRIDED && (y0 + y) % p.sy != 0) continue;
+          T1 Q0 = 0u, Q1 = 0u;
+          uint64_t Q2 = 0ull, Q3 = 0ull, Q4 = 0ull;
+          T1 R0[4], R1[4];
+          uint64_t R2[4], R3[4], R4[4];
+          const int plane = TY * G::VSP;
+#pragma unroll
+          for (int e = 0; e < 4 + KX - 1; e++) {
+            const int cidx = y * G::VSP + 4 * lane + e;
+            // (wide: the ky-row sums of X fit int32; their kx-column sums may not)
+            Q0 += WIDE ? (T1)(long long)(int)VS[0 * plane + cidx] : (T1)VS[0 * plane + cidx];
+            Q1 += WIDE ? (T1)(long long)(int)VS[1 * plane + cidx] : (T1)VS[1 * plane + cidx];
+            Q2 += (uint64_t)VS[2 * plane + cidx] | ((uint64_t)VS[3 * plane + cidx] << 32);
+            Q3 += (uint64_t)VS[4 * plane + cidx] | ((uint64_t)VS[5 * plane + cidx] << 32);
+            Q4 += (uint64_t)VS[6 * plane + cidx] | ((uint64_t)VS[7 * plane + cidx] << 32);
+            if (e <= 2) {
+              R0[e + 1] = Q0; R1[e + 1] = Q1; R2[e + 1] = Q2; R3[e + 1] = Q3; R4[e + 1] = Q4;
+            }
+            if (e >= KX - 1 && (!STRIDED || ((col_mask >> (e - (KX - 1))) & 1u))) {
+              const int c = e - (KX - 1);
+              V0[a][c] += Q0 - (c >= 1 ? R0[c] : (T1)0u);
+              V1[a][c] += Q1 - (c >= 1 ? R1[c] : (T1)0u);
+              V2[a][c] += Q2 - (c >= 1 ? R2[c] : 0ull);
+              V3[a][c] += Q3 - (c >= 1 ? R3[c] : 0ull);
+              V4[a][c] += Q4 - (c >= 1 ? R4[c] : 0ull);
+            }
           }
         }
-      }
+      };
+      if (p.unit_stride)
+        hpass(std::false_type{});
+      else
+        hpass(std::true_type{});
 
       // step 4 for the output plane whose window is complete: Eq. 2 from the
       // exact sums of window (a, c) with n in-volume cells; `fail` reports a
