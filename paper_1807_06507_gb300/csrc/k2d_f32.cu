@@ -44,11 +44,25 @@ __global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid
   sc.tmx_t = &p.tmx_t;
   sc.tmy_t = &p.tmy_t;
   uint32_t seq = 0;
-  for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-    const int rbi = item / sc.n_strips;
-    const int strip = item - rbi * sc.n_strips;
-    const int rb = p.rb0 + rbi;
-    if (!process_item_2d_f32<M, KW, TMA>(sc, strip, rb, rg, seq, p.status)) return;
+  // work items, or (second-tier launch) the tasks the previous launch listed
+  const int n_iter = sc.redo_mode == 2 ? min(*sc.redo_count, sc.redo_cap) : p.n_items;
+  for (int it = blockIdx.x; it < n_iter; it += gridDim.x) {
+    int strip, j0, j1, slot = 0;
+    uint32_t lanes = 0u;
+    if (sc.redo_mode == 2) {
+      const RedoTask2D t = sc.redo_tasks[it];
+      strip = t.strip;
+      j0 = t.j0;
+      j1 = t.j1;
+      lanes = t.lanes;
+      slot = t.range_slot;
+    } else {
+      const int rbi = it / sc.n_strips;
+      strip = it - rbi * sc.n_strips;
+      j0 = (p.rb0 + rbi) * sc.TJ;
+      j1 = min(j0 + sc.TJ, sc.OH);
+    }
+    if (!process_rows_2d_f32<M, KW, TMA>(sc, strip, j0, j1, lanes, slot, rg, seq, p.status)) return;
   }
 }
 

@@ -35,12 +35,16 @@
 //    data on a grid step of at most 1 convert exactly, rho = 0: nothing to
 //    test).  A window that does not pass flags its lane.  After the item,
 //    each flagged lane determines whether its values convert exactly (then
-//    its results stand); the others march their item again from L2 with a
+//    its results stand); the others march again through the ring with a
 //    finer map of the same range (up to 26 bits, 64-bit sums, Eq. 2 in
 //    128-bit integers), which certifies the windows of ordinary float data
-//    whose spread is small next to the lane's range.  Windows that still
-//    fail (a value orders of magnitude above its neighbours in the lane's
-//    columns) are recomputed from their own cells by the whole warp at once.
+//    whose spread is small next to the lane's range.  Plain plans list that
+//    second tier as tasks of a few output rows for a second launch, which
+//    spreads them over every SM (a few listed items no longer hold up the
+//    whole grid); batched plans and host-run bands run it inside the item.
+//    Windows that still fail (a value orders of magnitude above its
+//    neighbours in the lane's columns) are recomputed from their own cells
+//    by the whole warp at once.
 #pragma once
 
 #include <type_traits>
@@ -166,13 +170,16 @@ static __device__ __noinline__ void fix_listed_2d(FixScene2D sc, float* out, lon
   if (lane == 0 && n > 0) atomicAdd(status + ST_FALLBACK, (uint32_t)n);
 }
 
+// Output rows [j0, j1) of column strip `strip`.  sc.redo_mode 0 and 1: the
+// whole item (the second tier in place, or listed as tasks); 2: one
+// second-tier task, for the lanes in task_lanes (pass 2 is skipped).
 template <int M, int KW, bool TMA>
-__device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip, int rb, const Ring2DF& rg,
-                                                    uint32_t& seq, uint32_t* status) {
+__device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip, int j0, int j1, uint32_t task_lanes,
+                                                    int task_slot, const Ring2DF& rg, uint32_t& seq,
+                                                    uint32_t* status) {
   using G = Geo2DF<M, KW>;
   const int lane = threadIdx.x & 31;
-  const int j0 = rb * sc.TJ;
-  const int j1 = min(j0 + sc.TJ, sc.OH);
+  const bool task = sc.redo_mode == 2;
   const int t0 = j0 * sc.sy - sc.h1;
   const int nrows = (j1 - 1 - j0) * sc.sy + sc.kh;
   const int cstrip = strip * 32 * M;
@@ -272,7 +279,10 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   bool allint = true;  // every value an integer (then, with s >= 1, every value converts exactly)
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
-  if (!stream_rows(false, [&](int i, uint32_t s, auto) {
+  if (task) {  // a task re-marches with the ranges its item measured
+    const float4 r = sc.redo_ranges[32 * task_slot + lane];
+    xlo = r.x; xhi = r.y; ylo = r.z; yhi = r.w;
+  } else if (!stream_rows(false, [&](int i, uint32_t s, auto) {
         if (t0 + i < 0 || t0 + i >= sc.H) return;
         const float* px = lane_ptr(rg.rx, s);
         const float* py = lane_ptr(rg.ry, s);
@@ -339,7 +349,8 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   const uint32_t seq0 = seq;
 
   // ---- pass 2: the D-march on fixed-point values
-  const bool ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
+  bool ok = true;
+  if (!task) ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
     constexpr bool has_leave = decltype(leave_tag)::value;
     const int te = t0 + i, tl = te - sc.kh;
     const bool e_ok = te >= 0 && te < sc.H;
@@ -470,7 +481,11 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
   // sums of all M windows would not fit the registers).  Every window of the
   // lane is rewritten; those that still fail are listed for the warp.
   bool redo = false;
-  if (__any_sync(0xffffffffu, need)) {
+  if (task) {
+    // a task's lanes were found inexact by the launch that listed them; a
+    // channel constant over the task's cells leaves exact NaN results
+    redo = ((task_lanes >> lane) & 1u) && xlo < xhi && ylo < yhi;
+  } else if (__any_sync(0xffffffffu, need)) {
     const bool exact = exact_state == 1 ||
                        (need && exact_state < 0 &&
                         lane_exact_2d<G::NCOL>((const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, max(t0, 0),
@@ -478,6 +493,28 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
     // a channel constant over the lane's cells makes every window's variance
     // exactly zero: the item map's results (NaN) stand
     redo = need && !exact && xlo < xhi && ylo < yhi;
+    if (sc.redo_mode == 1) {
+      // list the item's second tier as tasks of redo_rows output rows for
+      // the next launch, which spreads them over every SM (the plan sizes
+      // the list for every item's tasks; a full list runs the tier here)
+      const uint32_t lanes = __ballot_sync(0xffffffffu, redo);
+      if (lanes) {
+        const int nt = (j1 - j0 + sc.redo_rows - 1) / sc.redo_rows;
+        int k = 0;
+        if (lane == 0) k = atomicAdd(sc.redo_count, nt);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k + nt <= sc.redo_cap) {
+          sc.redo_ranges[32 * k + lane] = make_float4(xlo, xhi, ylo, yhi);  // the first task's slot
+          if (lane < nt)
+            sc.redo_tasks[k + lane] =
+                RedoTask2D{strip, j0 + lane * sc.redo_rows, min(j0 + (lane + 1) * sc.redo_rows, j1), lanes, k, {0, 0, 0}};
+          for (int t = 32 + lane; t < nt; t += 32)
+            sc.redo_tasks[k + t] =
+                RedoTask2D{strip, j0 + t * sc.redo_rows, min(j0 + (t + 1) * sc.redo_rows, j1), lanes, k, {0, 0, 0}};
+          redo = false;
+        }
+      }
+    }
   }
   if (__any_sync(0xffffffffu, redo)) {
     if (lane == 0) *rg.npend = 0;
@@ -601,6 +638,13 @@ __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip
     fix_listed_2d<M>(fs, sc.out, sc.out_pitch, rg.pend, *rg.npend, ovf, cl, j0, j1, status);
   }
   return true;
+}
+
+template <int M, int KW, bool TMA>
+__device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip, int rb, const Ring2DF& rg,
+                                                    uint32_t& seq, uint32_t* status) {
+  const int j0 = rb * sc.TJ;
+  return process_rows_2d_f32<M, KW, TMA>(sc, strip, j0, min(j0 + sc.TJ, sc.OH), 0u, 0, rg, seq, status);
 }
 
 }  // namespace swc

@@ -15,6 +15,17 @@ enum : int {
 enum : uint32_t { ERRBIT_TIMEOUT = 1u, ERRBIT_BAD_ARG = 2u };
 
 
+// A float32 2-D second-tier task: the lanes `lanes` of column strip `strip`
+// re-march output rows [j0, j1) with a finer map (k2d_f32.cuh) of the value
+// ranges their item measured, kept at redo_ranges[32 * range_slot + lane].
+struct RedoTask2D {
+  int strip;
+  int j0, j1;
+  uint32_t lanes;
+  int range_slot;
+  int pad[3];
+};
+
 // One 2-D problem as the 2-D kernels see it.  All coordinates are input
 // cells; output (j_r, j_c) has centre (j_r * sy, j_c * sx).
 struct Scene2D {
@@ -41,6 +52,15 @@ struct Scene2D {
   int qbits;               // float32 path: fixed-point magnitude bits (|X| < 2^qbits)
   int wide;                // uint16 path: 64-bit second-moment sums (large windows)
   int test_stall;          // test hook: item (0, 0) never issues its first row's copy
+  // float32 second tier: 0 runs it inside the item; 1 lists it as tasks of
+  // at most redo_rows output rows (redo_tasks, redo_count, capacity
+  // redo_cap); 2 runs the listed tasks (the launch after a mode-1 launch)
+  int redo_mode;
+  int redo_rows;
+  int redo_cap;
+  RedoTask2D* redo_tasks;
+  int* redo_count;
+  float4* redo_ranges;     // (lo_x, hi_x, lo_y, hi_y) per listed item and lane
 };
 
 struct K2DParams {

@@ -311,7 +311,8 @@ struct swcorr_plan_s {
   int64_t cached_pitch = -1;
   // device status block
   uint32_t* d_status = nullptr;
-  // float32 3-D plans: count and list of the items left to the wide kernel
+  // float32 3-D plans: count and list of the items left to the wide kernel;
+  // float32 2-D plans: count and list of the second-tier tasks
   int* d_redo = nullptr;
   // batched plans: device block (scenes, tensor maps, items, counter), graph
   void* d_batch = nullptr;
@@ -753,6 +754,24 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     return cuda_fail(e, "cudaMemset(status)");
   }
   p->k2.status = p->d_status;
+  if (p->kind == KIND_2D_F32) {
+    // second-tier tasks of at most redo_rows output rows: every item can list
+    // all of its rows once, so the list never fills
+    Scene2D& sc = p->k2.sc;
+    // (short windows: short tasks spread a few listed items over many warps;
+    // tall windows: 2 kh rows keep the kh - 1 warm-up rows below half)
+    sc.redo_rows = sc.kh <= 8 ? 8 : 2 * sc.kh;
+    sc.redo_cap = p->k2.n_items * ((sc.TJ + sc.redo_rows - 1) / sc.redo_rows);
+    e = cudaMalloc(&p->d_redo, 256 + (size_t)sc.redo_cap * (sizeof(RedoTask2D) + 32 * sizeof(float4)));
+    if (e != cudaSuccess) {
+      swcorr_plan_destroy(p);
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "2-D task list: out of device memory")
+                                            : cuda_fail(e, "cudaMalloc(2-D task list)");
+    }
+    sc.redo_count = p->d_redo;
+    sc.redo_tasks = reinterpret_cast<RedoTask2D*>(reinterpret_cast<unsigned char*>(p->d_redo) + 256);
+    sc.redo_ranges = reinterpret_cast<float4*>(sc.redo_tasks + sc.redo_cap);
+  }
   if (p->kind == KIND_3D && p->dtype == SWCORR_F32) {
     e = cudaMalloc(&p->d_redo, ((size_t)p->k3.n_items + 1) * sizeof(int));
     if (e != cudaSuccess) {
@@ -805,8 +824,21 @@ static swcorr_status run_2d(swcorr_plan_s* p, const void* x, const void* y, cons
     p->cached_y = y;
     p->cached_pitch = ip;
   }
-  cudaError_t e = p->dtype == SWCORR_F32 ? k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma)
-                                         : k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
+  cudaError_t e;
+  if (p->dtype == SWCORR_F32 && p->d_redo) {
+    // the items list their second tier; a second launch spreads its tasks
+    // over every SM (it exits at once when nothing was listed)
+    K2DParams k2 = p->k2;
+    if ((e = cudaMemsetAsync(p->d_redo, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "2-D task list reset");
+    k2.sc.redo_mode = 1;
+    if ((e = k2d_f32_launch(k2.sc.kw, k2, p->grid, p->smem, st, use_tma)) != cudaSuccess)
+      return cuda_fail(e, "2-D kernel launch");
+    k2.sc.redo_mode = 2;
+    e = k2d_f32_launch(k2.sc.kw, k2, p->grid, p->smem, st, use_tma);
+  } else {
+    e = p->dtype == SWCORR_F32 ? k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma)
+                               : k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "2-D kernel launch");
   return SWCORR_OK;
 }
