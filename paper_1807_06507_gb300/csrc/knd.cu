@@ -14,8 +14,9 @@
 //    cells (a value <= -999 in x or y; such a cell adds 0 to the others).
 //    uint16 cells are X = x; float32 cells go through one fixed-point map of
 //    the whole grid (fxmap.cuh) taken from a range pass, with the same
-//    certificate as the fused kernels and an FP64 recomputation of the
-//    windows that fail it.  All sums are exact (modular) integers.
+//    certificate as the fused kernels; a window that fails it is recomputed
+//    from its own cells with a window-local map (26 bits, exact 64-bit sums),
+//    and in FP64 if that fails too.  All sums are exact (modular) integers.
 //  * Pass along dimension d: sliding sums over the clipped window
 //    [i - floor((k-1)/2), i + floor(k/2)] (outside cells add nothing); one
 //    thread per segment of a line (a running sum) for the outer dimensions,
@@ -318,6 +319,58 @@ static __device__ __noinline__ float nd_box_fp64(const KNDParams& p, const long 
   return 0.0f;
 }
 
+// Window-local recomputation over the n-dimensional box [lo, hi]: the box's
+// own range and map (fx_wide: up to 26 bits), exact 64-bit sums and Eq. 2 in
+// 128-bit integers, certified as the grid map's windows are.  False when the
+// certificate fails (the caller then takes nd_box_fp64).
+static __device__ __noinline__ bool nd_box_exact(const KNDParams& p, const long long* lo, const long long* hi,
+                                                 float* out) {
+  long long cur[KND_MAXDIM];
+  auto each = [&](auto&& fn) {
+    for (int d = 0; d < p.ndim; d++) cur[d] = lo[d];
+    while (true) {
+      long long off = 0;
+      for (int d = 0; d < p.ndim; d++) off += cur[d] * p.ipitch[d];
+      float a, b;
+      load_cell(p, off, a, b);
+      fn(a, b);
+      int d = p.ndim - 1;
+      for (; d >= 0; d--) {
+        if (cur[d] < hi[d]) {
+          cur[d]++;
+          break;
+        }
+        cur[d] = lo[d];
+      }
+      if (d < 0) break;
+    }
+  };
+  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
+  long long n = 0;
+  each([&](float a, float b) {
+    xlo = fminf(xlo, a); xhi = fmaxf(xhi, a); ylo = fminf(ylo, b); yhi = fmaxf(yhi, b);
+    n++;
+  });
+  if (xlo == xhi || ylo == yhi) {  // a constant channel: zero variance, exactly
+    *out = __int_as_float(0x7fc00000);
+    return true;
+  }
+  const FxWide wx = fx_wide(xlo, xhi, n), wy = fx_wide(ylo, yhi, n);
+  long long Sx = 0, Sy = 0, Sxx = 0, Syy = 0, Sxy = 0;
+  bool okx = true, oky = true;
+  each([&](float a, float b) {
+    const long long X = fx_wide_quant(a, wx, okx), Y = fx_wide_quant(b, wy, oky);
+    Sx += X; Sy += Y; Sxx += X * X; Syy += Y * Y; Sxy += X * Y;
+  });
+  const __int128 N = n;
+  const __int128 vx = N * Sxx - (__int128)Sx * Sx;
+  const __int128 vy = N * Syy - (__int128)Sy * Sy;
+  const __int128 num = N * Sxy - (__int128)Sx * Sy;
+  if (!fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, okx ? 0.0f : 0.5f, oky ? 0.0f : 0.5f)) return false;
+  *out = fx_pearson128(num, vx, vy);
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads) nd_finalize(KNDParams p, const long long* W) {
   const int* r = reinterpret_cast<const int*>(p.scratch);
   float rhox = 0.0f, rhoy = 0.0f;
@@ -384,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) nd_finalize(KNDParams p, const long 
     const __int128 num = N * S[4] - (__int128)S[0] * S[1];
     float c = fx_pearson128(num, vx, vy);  // a zero variance: 0 * rsqrt(0) = NaN
     if (p.is_f32 && !fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, rhox, rhoy)) {
-      c = nd_box_fp64(p, lo, hi);
+      if (!nd_box_exact(p, lo, hi, &c)) c = nd_box_fp64(p, lo, hi);
       recomputed++;
     }
     p.out[o] = c;

@@ -131,3 +131,24 @@ def test_cumulative_sum_ablation_equals_sliding(sw, dtype):
     ref, rx, ry = oracle.corr(x, y, k, st, relvar=True)
     score(c_sat, ref, rx, ry, exact_nan=(dtype == "u16"))
     score(c_nd, ref, rx, ry, exact_nan=(dtype == "u16"))
+
+
+@pytest.mark.parametrize("case", ["even_2d_scaled_night", "3d_unequal_spike"])
+def test_general_path_float32_high_dynamic_range(sw, case):
+    """Window shapes the fused kernels have no instance for run on the general
+    path, whose float32 map spans the whole grid; windows it cannot certify
+    are recomputed from their own cells (window-local map, then FP64)."""
+    from paper_1807_06507_gb300 import workloads as W
+    if case == "even_2d_scaled_night":
+        vis, ir = W.night_scene((200, 300), seed=16)
+        x, y, k = vis.astype(np.float32) * np.float32(0.37), ir.astype(np.float32), (8, 6)
+    else:
+        rng = np.random.default_rng(17)
+        x = rng.standard_normal((12, 30, 40)).astype(np.float32)
+        y = (0.5 * x + rng.standard_normal(x.shape)).astype(np.float32)
+        x[6, 15, 20] = np.float32(1e6)
+        k = (3, 5, 7)
+    c, _, fb = run(sw, x, y, k)
+    ref, rx, ry = oracle.corr(x, y, k, relvar=True)
+    score(c, ref, rx, ry, exact_nan=False)
+    assert fb > 0
