@@ -13,10 +13,10 @@ template <bool F32, bool UNIT>
 static cudaError_t launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st) {
   static std::atomic<uint64_t> attr_done{0};  // one bit per device
   cudaError_t e = once_per_device(attr_done, [] {
-    return cudaFuncSetAttribute(k1d_kernel<kM1, F32, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    return cudaFuncSetAttribute(k1d_kernel<kM1, F32, UNIT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
   if (e != cudaSuccess) return e;
-  k1d_kernel<kM1, F32, UNIT><<<grid, 32 * warps, smem, st>>>(p);
+  k1d_kernel<kM1, F32, UNIT, false><<<grid, 32 * warps, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -31,13 +31,13 @@ cudaError_t k1d_launch(const K1DParams& p, int grid, int warps, size_t smem, cud
 int k1d_blocks_per_sm(bool f32, int warps, size_t smem) {
   // the unit-stride and any-stride instances share launch bounds and layout
   int b = 0;
-  cudaError_t e = f32 ? cudaFuncSetAttribute(k1d_kernel<kM1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = f32 ? cudaFuncSetAttribute(k1d_kernel<kM1, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              220 * 1024)
-                      : cudaFuncSetAttribute(k1d_kernel<kM1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                      : cudaFuncSetAttribute(k1d_kernel<kM1, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              220 * 1024);
   if (e != cudaSuccess) return 0;
-  e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, true, true>, 32 * warps, smem)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, false, true>, 32 * warps, smem);
+  e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, true, true, false>, 32 * warps, smem)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1d_kernel<kM1, false, true, false>, 32 * warps, smem);
   return e == cudaSuccess ? b : 0;
 }
 

@@ -30,10 +30,13 @@
 //    stages them for coalesced stores.
 //  * float32 certificate (fxmap.cuh): a window passes when
 //    vx, vy >= (rho n / 4.5e-6)^2 (rho = 0 for a channel whose chunk
-//    converted exactly).  A lane with failing windows recomputes them after
-//    the stores with a map of its own span at up to 24 bits (64-bit sums,
-//    sliding from window to window); a window that still fails is recomputed
-//    from its own cells (fx_recompute).
+//    converted exactly).  A chunk with failing windows is listed; a second
+//    launch of this kernel in its wide form runs the listed chunks again
+//    with a map of up to 26 bits of the chunk's range (fx_wide), 64-bit
+//    first moments and Eq. 2 in 128-bit integers, rewriting every output of
+//    the chunk.  A lane whose windows still fail recomputes them from the
+//    chunk's floats with a map of its own span, sliding from window to
+//    window; a window that fails that too is recomputed from its own cells.
 #pragma once
 
 #include <type_traits>
@@ -94,6 +97,51 @@ struct Sums5 {
     return r;
   }
 };
+
+// The wide form's window sums: 64-bit first moments (values of up to 26
+// bits, fx_wide), all modular.
+struct Sums5W {
+  uint64_t x, y, xx, yy, xy;
+  __device__ __forceinline__ void zero() { x = y = xx = yy = xy = 0ull; }
+  __device__ __forceinline__ void add(int X, int Y) {
+    x += (uint64_t)(long long)X;
+    y += (uint64_t)(long long)Y;
+    xx += (uint64_t)((long long)X * X);
+    yy += (uint64_t)((long long)Y * Y);
+    xy += (uint64_t)((long long)X * Y);
+  }
+  __device__ __forceinline__ void slide(int Xi, int Yi, int Xo, int Yo) {
+    const int dx = Xi - Xo, dy = Yi - Yo;
+    x += (uint64_t)(long long)dx;
+    y += (uint64_t)(long long)dy;
+    xx += (uint64_t)((long long)dx * (Xi + Xo));
+    yy += (uint64_t)((long long)dy * (Yi + Yo));
+    xy += (uint64_t)((long long)dx * Yi + (long long)Xo * dy);
+  }
+  __device__ __forceinline__ void add(const Sums5W& o) { x += o.x; y += o.y; xx += o.xx; yy += o.yy; xy += o.xy; }
+  __device__ __forceinline__ void sub(const Sums5W& o) { x -= o.x; y -= o.y; xx -= o.xx; yy -= o.yy; xy -= o.xy; }
+  __device__ __forceinline__ Sums5W shfl(int src) const {
+    Sums5W r;
+    r.x = __shfl_sync(0xffffffffu, x, src);
+    r.y = __shfl_sync(0xffffffffu, y, src);
+    r.xx = __shfl_sync(0xffffffffu, xx, src);
+    r.yy = __shfl_sync(0xffffffffu, yy, src);
+    r.xy = __shfl_sync(0xffffffffu, xy, src);
+    return r;
+  }
+};
+
+// Eq. 2 of the wide form in 128-bit integers (sums of X^2 below 2^62), with
+// the precise certificate (rx, ry: the channels' rounding bounds).
+__device__ __forceinline__ float pearson_wide(const Sums5W& s, uint32_t n, float rx, float ry, bool& fail) {
+  const __int128 N = n;
+  const long long sx = (long long)s.x, sy = (long long)s.y;
+  const __int128 vx = N * (long long)s.xx - (__int128)sx * sx;
+  const __int128 vy = N * (long long)s.yy - (__int128)sy * sy;
+  const __int128 num = N * (long long)s.xy - (__int128)sx * sy;
+  fail = !fx_certified(i128_to_f32(vx), i128_to_f32(vy), (float)n, rx, ry);
+  return fx_pearson128(num, vx, vy);
+}
 
 // Eq. 2 from exact modular window sums (the results fit in int64; the first
 // moments are below 2^31 in magnitude).  fail: the float32 certificate's
@@ -223,8 +271,13 @@ static __device__ __noinline__ void lane_redo_1d(const float* sx_span, const flo
   if (count) atomicAdd(status + ST_FALLBACK, count);
 }
 
-template <int M1, bool F32, bool UNIT>
+// WIDE = true (float32 only): the second tier, run on the chunks the first
+// launch listed, with a map of up to 26 bits of the chunk's range (fx_wide),
+// 64-bit first moments and Eq. 2 in 128-bit integers.
+template <int M1, bool F32, bool UNIT, bool WIDE>
 __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1DParams p) {
+  static_assert(F32 || !WIDE, "the wide form is float32 only");
+  using S5 = std::conditional_t<WIDE, Sums5W, Sums5>;
   constexpr int LW = 32 * M1;  // outputs per warp
   static_assert(LW % 4 == 0, "vector stores of the staged outputs");
   using T = typename std::conditional<F32, float, uint16_t>::type;
@@ -256,7 +309,9 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
   const int seg = M1 * (UNIT ? 1 : p.stride);
   const int ncell = p.nbox * 256;
 
-  for (long long item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+  const long long n_iter = WIDE ? (long long)*p.redo_count : p.n_items;
+  for (long long it = blockIdx.x; it < n_iter; it += gridDim.x) {
+    const long long item = WIDE ? p.redo_items[it] : it;
     const long long c0 = item * L;                   // first output of the chunk
     const long long e_first = c0 * p.stride - p.h1;  // first cell of its windows
     const long long e0 = e_first >= 0 ? e_first / kAlign * kAlign : -((-e_first + kAlign - 1) / kAlign) * kAlign;
@@ -292,6 +347,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
 
     // ---- float32: fixed point of the chunk, converted in place
     float Kx = 0.0f, Ky = 0.0f;  // certificate thresholds (0: exact, or uint16)
+    float wrx = 0.0f, wry = 0.0f;  // wide form: rounding bounds (0: every value on the grid)
     if constexpr (F32) {
       float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f;
       const float4* X4 = reinterpret_cast<const float4*>(X);
@@ -337,9 +393,31 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
         ylo = fminf(ylo, red[2 * nw + w]);
         yhi = fmaxf(yhi, red[3 * nw + w]);
       }
-      const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
       int4* XW = reinterpret_cast<int4*>(X);
       int4* YW = reinterpret_cast<int4*>(Y);
+      if constexpr (WIDE) {
+        // X = round(x s) - M through a 64-bit conversion (x s is exact)
+        const FxWide wx = fx_wide(xlo, xhi, p.k), wy = fx_wide(ylo, yhi, p.k);
+        const bool const_ch = !(xlo < xhi) || !(ylo < yhi);  // a constant channel: every window NaN
+        bool gx = true, gy = true;
+        for (int v = tid; v < ncell / 4; v += blockDim.x) {
+          const int e = 4 * v;
+          const float4 a = X4[v], b = Y4[v];
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+          int ia[4], ib[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const bool on = !const_ch && e + u >= v_lo && e + u < v_hi;
+            ia[u] = on ? (int)fx_wide_quant(av[u], wx, gx) : 0;
+            ib[u] = on ? (int)fx_wide_quant(bv[u], wy, gy) : 0;
+          }
+          XW[v] = make_int4(ia[0], ia[1], ia[2], ia[3]);
+          YW[v] = make_int4(ib[0], ib[1], ib[2], ib[3]);
+        }
+        wrx = __syncthreads_or(!gx) ? 0.5f : 0.0f;
+        wry = __syncthreads_or(!gy) ? 0.5f : 0.0f;
+      } else {
+      const FxMap qx = fx_make(xlo, xhi, p.qbits), qy = fx_make(ylo, yhi, p.qbits);
       // conversion in place; rx, ry: largest rounding residual of an on-series value
       float rx = 0.0f, ry = 0.0f;
       auto cv = [&](float v, const FxMap& q, float& racc, bool on) {
@@ -372,11 +450,12 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
       const float k0 = 4.9432e10f * (float)p.k * (float)p.k;  // (1 / 4.5e-6)^2 * 1.001 * n^2
       Kx = inexact_x ? k0 * qx.rho * qx.rho : 0.0f;
       Ky = inexact_y ? k0 * qy.rho * qy.rho : 0.0f;
+      }
     }
 
     // ---- this warp's outputs: segment sums, first windows, slide
     const int woff = off + warp * LW * p.stride;  // span offset of the warp's first window
-    Sums5 Tt[2], R[2];
+    S5 Tt[2], R[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       Tt[h].zero();
@@ -393,32 +472,32 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
       for (; u < nc; u++) Tt[h].add((int)XI[b + u], (int)YI[b + u]);
     }
     // inclusive scan of the 64 segment totals (lanes, then the second half)
-    Sums5 C0 = Tt[0], C1 = Tt[1];
+    S5 C0 = Tt[0], C1 = Tt[1];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const Sums5 a = C0.shfl(max(lane - o, 0)), b = C1.shfl(max(lane - o, 0));
+      const S5 a = C0.shfl(max(lane - o, 0)), b = C1.shfl(max(lane - o, 0));
       if (lane >= o) {
         C0.add(a);
         C1.add(b);
       }
     }
-    const Sums5 tot0 = C0.shfl(31);
+    const S5 tot0 = C0.shfl(31);
     C1.add(tot0);
     // first window of lane j: segments j .. j+q-1 plus the first r cells of j+q
     // = C(j+q-1) - C(j-1) + R(j+q)
-    auto pick_C = [&](int g) -> Sums5 {  // C(g) for g in [-1, 63], uniform-safe shuffles
-      Sums5 a = C0.shfl(g & 31), b = C1.shfl(g & 31);
+    auto pick_C = [&](int g) -> S5 {  // C(g) for g in [-1, 63], uniform-safe shuffles
+      S5 a = C0.shfl(g & 31), b = C1.shfl(g & 31);
       if (g < 0) {
         a.zero();
         return a;
       }
       return g < 32 ? a : b;
     };
-    auto pick_R = [&](int g) -> Sums5 {
-      Sums5 a = R[0].shfl(g & 31), b = R[1].shfl(g & 31);
+    auto pick_R = [&](int g) -> S5 {
+      S5 a = R[0].shfl(g & 31), b = R[1].shfl(g & 31);
       return g < 32 ? a : b;
     };
-    Sums5 W = pick_C(lane + p.q - 1);
+    S5 W = pick_C(lane + p.q - 1);
     W.sub(pick_C(lane - 1));
     W.add(pick_R(lane + p.q));
 
@@ -440,7 +519,10 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
 #pragma unroll
       for (int t = 0; t < M1; t++) {
         bool f;
-        res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
+        if constexpr (WIDE)
+          res[t] = pearson_wide(W, n_of(j_base + t), wrx, wry, f);
+        else
+          res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
         fail |= (uint64_t)f << t;
         if constexpr (!F32) emit_sums(p, W, j_base + t);
         if (t + 1 < M1) {
@@ -453,7 +535,10 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
 #pragma unroll
       for (int t = 0; t < M1; t++) {
         bool f;
-        res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
+        if constexpr (WIDE)
+          res[t] = pearson_wide(W, n_of(j_base + t), wrx, wry, f);
+        else
+          res[t] = pearson_exact(W, n_of(j_base + t), Kx, Ky, f);
         fail |= (uint64_t)f << t;
         if constexpr (!F32) emit_sums(p, W, j_base + t);
         if (t + 1 < M1) {
@@ -483,15 +568,21 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     } else {
       for (int u = lane; u < nvalid; u += 32) dst[u] = sw[u];
     }
-    if constexpr (F32) {
-      // lanes with failing windows recompute them from the chunk's floats,
-      // loaded again into the span buffer once every warp has stored
+    if constexpr (WIDE) {
+      // every output of the chunk was rewritten; lanes with windows that
+      // still fail recompute them from the chunk's floats, loaded again into
+      // the span buffer once every warp has stored
+      if (lane == 0 && nvalid > 0) atomicAdd(p.status + ST_FALLBACK, (uint32_t)nvalid);
       if (__syncthreads_or(fail != 0ull)) {
         if (!load_span()) return;
         if (fail)
           lane_redo_1d(reinterpret_cast<const float*>(X), reinterpret_cast<const float*>(Y), e0, p.N, p.k, p.h1, p.h2,
                        p.stride, j_base, fail, p.n_out, p.out, p.status);
       }
+    } else if constexpr (F32) {
+      // a chunk with failing windows (its values do not all convert exactly,
+      // or no window could fail) is listed for the wide launch
+      if (__syncthreads_or(fail != 0ull) && tid == 0) p.redo_items[atomicAdd(p.redo_count, 1)] = item;
     }
     __syncthreads();  // the span is reused by the next chunk
   }

@@ -27,6 +27,10 @@ struct K1DParams {
   float* out;
   long long* sums;   // optional (uint16): 5 int64 per output, Sx Sy Sxx Syy Sxy
   uint32_t* status;
+  // float32: chunks whose windows the chunk's map left uncertified (the
+  // first launch appends them; the wide launch re-slides them)
+  int* redo_count;
+  long long* redo_items;
 };
 
 }  // namespace swc

@@ -27,6 +27,8 @@ cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cu
 // 1-D (uint16 or float32): outputs per lane per chunk, and the launch.
 int k1d_outputs_per_lane();
 cudaError_t k1d_launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st);
+// float32 second tier: the wide form over the chunks the first launch listed
+cudaError_t k1d_wide_launch(const K1DParams& p, int grid, int warps, size_t smem, cudaStream_t st);
 // resident CTAs of `warps` warps per SM with `smem` bytes (0 if the query fails)
 int k1d_blocks_per_sm(bool f32, int warps, size_t smem);
 

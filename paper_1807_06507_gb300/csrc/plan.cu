@@ -440,8 +440,20 @@ static swcorr_status run_1d(swcorr_plan_s* p, const void* x, const void* y, floa
   k1.ry = y;
   k1.out = c;
   k1.status = p->d_status;
-  cudaError_t e = k1d_launch(k1, p->grid, p->warps, p->smem, st);
+  cudaError_t e;
+  if (p->dtype == SWCORR_F32) {
+    // chunks the chunk map leaves uncertified go to the wide launch
+    k1.redo_count = p->d_redo;
+    k1.redo_items = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(p->d_redo) + 8);
+    if ((e = cudaMemsetAsync(p->d_redo, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "1-D chunk list reset");
+  } else {
+    k1.redo_count = nullptr;
+    k1.redo_items = nullptr;
+  }
+  e = k1d_launch(k1, p->grid, p->warps, p->smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "1-D kernel launch");
+  if (p->dtype == SWCORR_F32 && (e = k1d_wide_launch(k1, p->grid, p->warps, p->smem, st)) != cudaSuccess)
+    return cuda_fail(e, "1-D wide kernel launch");
   return SWCORR_OK;
 }
 
@@ -771,6 +783,14 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     sc.redo_count = p->d_redo;
     sc.redo_tasks = reinterpret_cast<RedoTask2D*>(reinterpret_cast<unsigned char*>(p->d_redo) + 256);
     sc.redo_ranges = reinterpret_cast<float4*>(sc.redo_tasks + sc.redo_cap);
+  }
+  if (p->kind == KIND_1D && p->dtype == SWCORR_F32) {
+    e = cudaMalloc(&p->d_redo, 8 + (size_t)p->k1.n_items * sizeof(long long));
+    if (e != cudaSuccess) {
+      swcorr_plan_destroy(p);
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "1-D chunk list: out of device memory")
+                                            : cuda_fail(e, "cudaMalloc(1-D chunk list)");
+    }
   }
   if (p->kind == KIND_3D && p->dtype == SWCORR_F32) {
     e = cudaMalloc(&p->d_redo, ((size_t)p->k3.n_items + 1) * sizeof(int));
