@@ -105,7 +105,7 @@ static __device__ __noinline__ bool lane_exact_2d(const float* gx, const float* 
                                                   int c0, int e_lo, int e_hi, FxMap qx, FxMap qy) {
   for (int pass = (qx.s >= 1.0f && qy.s >= 1.0f) ? 0 : 1; pass < 2; pass++) {
     bool ok = true;
-    for (int r = r0; r < r1; r++) {
+    for (int r = r0; r < r1 && ok; r++) {  // (a lane stops at its first value off the grid)
       const long long o = (long long)r * pitch + c0;
       float vx[NCOL], vy[NCOL];
 #pragma unroll
@@ -524,9 +524,15 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
     bool ongx = true, ongy = true;  // every value read so far lies on its channel's grid
     bool ovf = false;
     uint32_t count = 0;
+    // Windows up to 15 columns wide march all M windows in one pass: a row's
+    // first-moment contribution to a window, |sum of D| < 15 * 2^27.02, fits
+    // in 32 bits, which leaves registers for the 64-bit running sums.  Wider
+    // windows take two passes of M/2 windows.
+    constexpr int PARTS = KW <= 15 ? 1 : 2;
+    using T1 = std::conditional_t<PARTS == 1, uint32_t, unsigned long long>;
     auto redo_pass = [&](auto half_tag) -> bool {
       constexpr int HALF = decltype(half_tag)::value;
-      constexpr int MH = M / 2, NC = MH + KW - 1, EB = HALF * MH;  // lane columns [EB, EB + NC)
+      constexpr int MH = M / PARTS, NC = MH + KW - 1, EB = HALF * MH;  // lane columns [EB, EB + NC)
       constexpr int HB = (G::E0 + EB) / 4, HE = (G::E0 + EB + NC - 1) / 4 + 1;
       unsigned long long V[MH][5];
 #pragma unroll
@@ -545,8 +551,16 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
           const float* pye = lane_ptr(rg.ry, s);
           const float* pxl = lane_ptr(rg.lx, s);
           const float* pyl = lane_ptr(rg.ly, s);
-          unsigned long long P[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
-          unsigned long long Ps[MH > 1 ? MH - 1 : 1][5];
+          T1 P01[2] = {0u, 0u};
+          unsigned long long P[5] = {0ull, 0ull, 0ull, 0ull, 0ull};  // (entries 2-4 used)
+          T1 Ps01[MH > 1 ? MH - 1 : 1][2];
+          unsigned long long Ps[MH > 1 ? MH - 1 : 1][5];              // (entries 2-4 used)
+          auto ext = [](T1 v) -> unsigned long long {  // a row contribution, sign-extended
+            if constexpr (sizeof(T1) == 4)
+              return (unsigned long long)(long long)(int)v;
+            else
+              return v;
+          };
 #pragma unroll
           for (int h = HB; h < HE; h++) {
             const float4 a = *reinterpret_cast<const float4*>(pxe + 4 * h);
@@ -575,20 +589,24 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
               // |X| < 2^26 (1 + 2^-6) + 1: differences, sums and their
               // products fit 32 x 32 -> 64-bit multiplies
               const int D = (int)(Xe - Xl), S = (int)(Xe + Xl), Dy = (int)(Ye - Yl), Sy = (int)(Ye + Yl);
-              P[0] += (unsigned long long)(long long)D;
-              P[1] += (unsigned long long)(long long)Dy;
+              P01[0] += (T1)(long long)D;
+              P01[1] += (T1)(long long)Dy;
               P[2] += (unsigned long long)((long long)D * S);
               P[3] += (unsigned long long)((long long)Dy * Sy);
               P[4] += (unsigned long long)((long long)D * (int)Ye + (long long)(int)Xl * Dy);
               const int j = e - EB;
               if (j >= KW - 1) {
                 const int c = j - (KW - 1);
+                V[c][0] += ext(P01[0] - (c >= 1 ? Ps01[c - 1][0] : (T1)0u));
+                V[c][1] += ext(P01[1] - (c >= 1 ? Ps01[c - 1][1] : (T1)0u));
 #pragma unroll
-                for (int t = 0; t < 5; t++) V[c][t] += P[t] - (c >= 1 ? Ps[c - 1][t] : 0ull);
+                for (int t = 2; t < 5; t++) V[c][t] += P[t] - (c >= 1 ? Ps[c - 1][t] : 0ull);
               }
               if (j <= MH - 2) {
+                Ps01[j][0] = P01[0];
+                Ps01[j][1] = P01[1];
 #pragma unroll
-                for (int t = 0; t < 5; t++) Ps[j][t] = P[t];
+                for (int t = 2; t < 5; t++) Ps[j][t] = P[t];
               }
             }
           }
@@ -630,7 +648,8 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
       });
     };
     if (!redo_pass(std::integral_constant<int, 0>{})) return false;
-    if (!redo_pass(std::integral_constant<int, 1>{})) return false;
+    if constexpr (PARTS == 2)
+      if (!redo_pass(std::integral_constant<int, 1>{})) return false;
     if (count) atomicAdd(status + ST_FALLBACK, count);
     __syncwarp();
     const FixScene2D fs{(const float*)sc.gx, (const float*)sc.gy, sc.in_pitch, sc.H, sc.W, sc.h1, sc.h2, sc.kh, KW,
