@@ -1,81 +1,10 @@
-// k2d_f32.cu -- kernel entry points and instantiations of the fused 2-D
-// float32 correlation (one warp per CTA, persistent over work items).
+// k2d_f32.cu -- geometry and launch dispatch of the fused 2-D float32
+// correlation (one warp per CTA, persistent over work items); the kernel's
+// instances live in k2d_f32_p0.cu .. k2d_f32_p3.cu.
 #include "k2d_f32.cuh"
-#include "devonce.h"
 #include "launch.h"
 
 namespace swc {
-
-#ifndef SWC_K2DF_MINB
-#define SWC_K2DF_MINB 12  // resident one-warp CTAs per SM the float32 2-D kernel is compiled for
-#endif
-template <int M, int KW, bool TMA>
-__global__ void __launch_bounds__(32, SWC_K2DF_MINB) k2d_f32_kernel(const __grid_constant__ K2DParams p) {
-  using G = Geo2DF<M, KW>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Ring2DF rg;
-  rg.NR = p.NR;
-  rg.PF = p.PF;
-  rg.rx = reinterpret_cast<float*>(smem_raw);
-  rg.ry = rg.rx + (size_t)p.NR * G::RWS;
-  rg.lx = rg.ry + (size_t)p.NR * G::RWS;
-  rg.ly = rg.lx + (size_t)p.NR * G::RWS;
-  rg.bar = reinterpret_cast<uint64_t*>(rg.ly + (size_t)p.NR * G::RWS);
-  __shared__ uint32_t pend[kPend2D];  // windows the lane re-march could not certify
-  __shared__ int npend;
-  rg.pend = pend;
-  rg.npend = &npend;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < p.NR; s++) mbar_init(rg.bar + s, 1);
-    fence_mbar_init();
-    if (TMA) {
-      prefetch_tmap(&p.tmx);
-      prefetch_tmap(&p.tmy);
-      if (G::TAIL > 0) {
-        prefetch_tmap(&p.tmx_t);
-        prefetch_tmap(&p.tmy_t);
-      }
-    }
-  }
-  __syncwarp();
-  Scene2D sc = p.sc;
-  sc.tmx = &p.tmx;
-  sc.tmy = &p.tmy;
-  sc.tmx_t = &p.tmx_t;
-  sc.tmy_t = &p.tmy_t;
-  uint32_t seq = 0;
-  // work items, or (second-tier launch) the tasks the previous launch listed
-  const int n_iter = sc.redo_mode == 2 ? min(*sc.redo_count, sc.redo_cap) : p.n_items;
-  for (int it = blockIdx.x; it < n_iter; it += gridDim.x) {
-    int strip, j0, j1, slot = 0;
-    uint32_t lanes = 0u;
-    if (sc.redo_mode == 2) {
-      const RedoTask2D t = sc.redo_tasks[it];
-      strip = t.strip;
-      j0 = t.j0;
-      j1 = t.j1;
-      lanes = t.lanes;
-      slot = t.range_slot;
-    } else {
-      const int rbi = it / sc.n_strips;
-      strip = it - rbi * sc.n_strips;
-      j0 = (p.rb0 + rbi) * sc.TJ;
-      j1 = min(j0 + sc.TJ, sc.OH);
-    }
-    if (!process_rows_2d_f32<M, KW, TMA>(sc, strip, j0, j1, lanes, slot, rg, seq, p.status)) return;
-  }
-}
-
-template <int M, int KW, bool TMA>
-static cudaError_t launch_t(const K2DParams& p, int grid, size_t smem, cudaStream_t st) {
-  static std::atomic<uint64_t> attr_done{0};  // one bit per device
-  cudaError_t e = once_per_device(attr_done, [] {
-    return cudaFuncSetAttribute(k2d_f32_kernel<M, KW, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  });
-  if (e != cudaSuccess) return e;
-  k2d_f32_kernel<M, KW, TMA><<<grid, 32, smem, st>>>(p);
-  return cudaGetLastError();
-}
 
 template <int M, int KW>
 static void geo(Geo2DInfo* g) {
@@ -105,15 +34,11 @@ bool k2d_f32_geometry(int kw, Geo2DInfo* g) {
 }
 
 cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
-  switch (kw) {
-#define X(M, KW) \
-  case KW:       \
-    return tma ? launch_t<M, KW, true>(p, grid, smem, st) : launch_t<M, KW, false>(p, grid, smem, st);
-    SWC_K2DF_CASES(X)
-#undef X
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (kw < 1 || kw > 31 || kw % 2 == 0) return cudaErrorInvalidValue;
+  if (kw <= 7) return k2d_f32_launch_p0(kw, p, grid, smem, st, tma);
+  if (kw <= 15) return k2d_f32_launch_p1(kw, p, grid, smem, st, tma);
+  if (kw <= 23) return k2d_f32_launch_p2(kw, p, grid, smem, st, tma);
+  return k2d_f32_launch_p3(kw, p, grid, smem, st, tma);
 }
 
 }  // namespace swc

@@ -504,13 +504,11 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
         if (lane == 0) k = atomicAdd(sc.redo_count, nt);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k + nt <= sc.redo_cap) {
-          sc.redo_ranges[32 * k + lane] = make_float4(xlo, xhi, ylo, yhi);  // the first task's slot
-          if (lane < nt)
-            sc.redo_tasks[k + lane] =
-                RedoTask2D{strip, j0 + lane * sc.redo_rows, min(j0 + (lane + 1) * sc.redo_rows, j1), lanes, k, {0, 0, 0}};
-          for (int t = 32 + lane; t < nt; t += 32)
+          const int slot = (j0 / sc.TJ) * sc.n_strips + strip;  // the item's index (plain plans: one launch)
+          sc.redo_ranges[32 * slot + lane] = make_float4(xlo, xhi, ylo, yhi);
+          for (int t = lane; t < nt; t += 32)
             sc.redo_tasks[k + t] =
-                RedoTask2D{strip, j0 + t * sc.redo_rows, min(j0 + (t + 1) * sc.redo_rows, j1), lanes, k, {0, 0, 0}};
+                RedoTask2D{strip, j0 + t * sc.redo_rows, min(j0 + (t + 1) * sc.redo_rows, j1), lanes, slot, {0, 0, 0}};
           redo = false;
         }
       }

@@ -17,7 +17,8 @@ enum : uint32_t { ERRBIT_TIMEOUT = 1u, ERRBIT_BAD_ARG = 2u };
 
 // A float32 2-D second-tier task: the lanes `lanes` of column strip `strip`
 // re-march output rows [j0, j1) with a finer map (k2d_f32.cuh) of the value
-// ranges their item measured, kept at redo_ranges[32 * range_slot + lane].
+// ranges their item measured, kept at redo_ranges[32 * range_slot + lane]
+// (range_slot: the item's index).
 struct RedoTask2D {
   int strip;
   int j0, j1;
@@ -60,7 +61,7 @@ struct Scene2D {
   int redo_cap;
   RedoTask2D* redo_tasks;
   int* redo_count;
-  float4* redo_ranges;     // (lo_x, hi_x, lo_y, hi_y) per listed item and lane
+  float4* redo_ranges;     // (lo_x, hi_x, lo_y, hi_y) per item and lane
 };
 
 struct K2DParams {

@@ -23,6 +23,11 @@ int k2d_u16_blocks_per_sm(int kw, bool wide, size_t smem);
 // 2-D float32: same interface.
 bool k2d_f32_geometry(int kw, Geo2DInfo* g);
 cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+// the instances of four groups of window widths (1-7, 9-15, 17-23, 25-31)
+cudaError_t k2d_f32_launch_p0(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+cudaError_t k2d_f32_launch_p1(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+cudaError_t k2d_f32_launch_p2(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+cudaError_t k2d_f32_launch_p3(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
 
 // 1-D (uint16 or float32): outputs per lane per chunk, and the launch.
 int k1d_outputs_per_lane();
@@ -43,6 +48,11 @@ cudaError_t kbatched_launch(const KBatchParams& p, int cls, int grid, size_t sme
 int kbatched_f32_ring_row();
 const void* kbatched_f32_kernel_ptr(int cls);
 cudaError_t kbatched_f32_prepare();
+// the instances of two groups of window widths (1-15, 17-31), by width
+const void* kbatched_f32_kernel_ptr_p0(int kw);
+const void* kbatched_f32_kernel_ptr_p1(int kw);
+cudaError_t kbatched_f32_launch_p0(int kw, const KBatchParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t kbatched_f32_launch_p1(int kw, const KBatchParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t kbatched_f32_launch(const KBatchParams& p, int cls, int grid, size_t smem, cudaStream_t st);
 
 // 3-D (uint16 or float32), square in-plane windows ky = kx = k.

@@ -774,7 +774,8 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     // tall windows: 2 kh rows keep the kh - 1 warm-up rows below half)
     sc.redo_rows = sc.kh <= 8 ? 8 : 2 * sc.kh;
     sc.redo_cap = p->k2.n_items * ((sc.TJ + sc.redo_rows - 1) / sc.redo_rows);
-    e = cudaMalloc(&p->d_redo, 256 + (size_t)sc.redo_cap * (sizeof(RedoTask2D) + 32 * sizeof(float4)));
+    e = cudaMalloc(&p->d_redo, 256 + (size_t)sc.redo_cap * sizeof(RedoTask2D) +
+                                   (size_t)p->k2.n_items * 32 * sizeof(float4));
     if (e != cudaSuccess) {
       swcorr_plan_destroy(p);
       return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "2-D task list: out of device memory")
