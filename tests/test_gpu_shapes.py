@@ -70,3 +70,27 @@ def test_shape_matches_oracle(sw, shape, k, stride, dtype):
     else:
         ref, rx, ry = oracle.corr(x, y, k, stride, relvar=True)
         score(c, ref, rx, ry, exact_nan=False)
+
+
+def hdr_pair(shape, seed):
+    """float32 off the integers with sparse cells 10^4 times the background:
+    most blocks need the second tier, at every border geometry."""
+    rng = np.random.default_rng(seed)
+    x = (0.37 * (100.0 + rng.standard_normal(shape))).astype(np.float32)
+    y = (0.5 * x + 0.3 * rng.standard_normal(shape)).astype(np.float32)
+    flat = x.reshape(-1)
+    flat[rng.integers(0, flat.size, max(1, flat.size // 3000))] = np.float32(3.7e5)
+    return x, y
+
+
+HDR_CASES = [((1, 500), (7, 7), None), ((3, 701), (7, 7), None), ((17, 2049), (9, 31), (2, 3)),
+             ((40, 263), (5, 13), None), ((2, 9, 131), (9, 9, 9), None), ((6, 21, 77), (5, 5, 5), (2, 2, 2)),
+             ((1500,), 1001, None), ((20_000,), 999, (3,))]
+
+
+@pytest.mark.parametrize("shape,k,stride", HDR_CASES)
+def test_fused_float32_second_tier_at_edges(sw, shape, k, stride):
+    x, y = hdr_pair(shape, len(shape) * 7 + sum(np.atleast_1d(k)))
+    c, _ = run(sw, x, y, k, stride)
+    ref, rx, ry = oracle.corr(x, y, k, stride, relvar=True)
+    score(c, ref, rx, ry, exact_nan=False)
