@@ -1,6 +1,6 @@
 // k2d_f32.cu -- geometry and launch dispatch of the fused 2-D float32
 // correlation (one warp per CTA, persistent over work items); the kernel's
-// instances live in k2d_f32_p0.cu .. k2d_f32_p3.cu.
+// instances live in k2d_f32_p0.cu .. k2d_f32_p7.cu.
 #include "k2d_f32.cuh"
 #include "launch.h"
 
@@ -33,12 +33,18 @@ bool k2d_f32_geometry(int kw, Geo2DInfo* g) {
   }
 }
 
-cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma) {
+cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier) {
   if (kw < 1 || kw > 31 || kw % 2 == 0) return cudaErrorInvalidValue;
-  if (kw <= 7) return k2d_f32_launch_p0(kw, p, grid, smem, st, tma);
-  if (kw <= 15) return k2d_f32_launch_p1(kw, p, grid, smem, st, tma);
-  if (kw <= 23) return k2d_f32_launch_p2(kw, p, grid, smem, st, tma);
-  return k2d_f32_launch_p3(kw, p, grid, smem, st, tma);
+  switch ((kw - 1) / 4) {  // the part holding this width
+    case 0: return k2d_f32_launch_p0(kw, p, grid, smem, st, tma, tier);
+    case 1: return k2d_f32_launch_p1(kw, p, grid, smem, st, tma, tier);
+    case 2: return k2d_f32_launch_p2(kw, p, grid, smem, st, tma, tier);
+    case 3: return k2d_f32_launch_p3(kw, p, grid, smem, st, tma, tier);
+    case 4: return k2d_f32_launch_p4(kw, p, grid, smem, st, tma, tier);
+    case 5: return k2d_f32_launch_p5(kw, p, grid, smem, st, tma, tier);
+    case 6: return k2d_f32_launch_p6(kw, p, grid, smem, st, tma, tier);
+    default: return k2d_f32_launch_p7(kw, p, grid, smem, st, tma, tier);
+  }
 }
 
 }  // namespace swc

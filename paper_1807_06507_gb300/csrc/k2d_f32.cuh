@@ -170,16 +170,23 @@ static __device__ __noinline__ void fix_listed_2d(FixScene2D sc, float* out, lon
   if (lane == 0 && n > 0) atomicAdd(status + ST_FALLBACK, (uint32_t)n);
 }
 
-// Output rows [j0, j1) of column strip `strip`.  sc.redo_mode 0 and 1: the
-// whole item (the second tier in place, or listed as tasks); 2: one
-// second-tier task, for the lanes in task_lanes (pass 2 is skipped).
-template <int M, int KW, bool TMA>
+// The second tier's placement, a compile-time choice so that each kernel
+// instance holds the registers of the passes it runs.
+enum : int {
+  TIER_IN_PLACE = 0,  // the whole item, second tier inside it (batched plans, host-run bands)
+  TIER_LIST = 1,      // the item's first tier; its second tier listed as tasks
+  TIER_TASK = 2       // one listed task: the second tier only
+};
+
+// Output rows [j0, j1) of column strip `strip` (TIER_TASK: the lanes in
+// task_lanes, with the ranges of their item at range slot task_slot).
+template <int M, int KW, bool TMA, int TIER>
 __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip, int j0, int j1, uint32_t task_lanes,
                                                     int task_slot, const Ring2DF& rg, uint32_t& seq,
                                                     uint32_t* status) {
   using G = Geo2DF<M, KW>;
   const int lane = threadIdx.x & 31;
-  const bool task = sc.redo_mode == 2;
+  constexpr bool task = TIER == TIER_TASK;
   const int t0 = j0 * sc.sy - sc.h1;
   const int nrows = (j1 - 1 - j0) * sc.sy + sc.kh;
   const int cstrip = strip * 32 * M;
@@ -279,7 +286,7 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
   bool allint = true;  // every value an integer (then, with s >= 1, every value converts exactly)
   // in-grid columns of the lane: e in [e_lo, e_hi)
   const int e_lo = max(0, G::W1 - cl), e_hi = min(G::NCOL, sc.W - (cl - G::W1));
-  if (task) {  // a task re-marches with the ranges its item measured
+  if constexpr (task) {  // a task re-marches with the ranges its item measured
     const float4 r = sc.redo_ranges[32 * task_slot + lane];
     xlo = r.x; xhi = r.y; ylo = r.z; yhi = r.w;
   } else if (!stream_rows(false, [&](int i, uint32_t s, auto) {
@@ -350,7 +357,7 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
 
   // ---- pass 2: the D-march on fixed-point values
   bool ok = true;
-  if (!task) ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
+  if constexpr (!task) ok = stream_rows(true, [&](int i, uint32_t s, auto leave_tag) {
     constexpr bool has_leave = decltype(leave_tag)::value;
     const int te = t0 + i, tl = te - sc.kh;
     const bool e_ok = te >= 0 && te < sc.H;
@@ -481,7 +488,7 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
   // sums of all M windows would not fit the registers).  Every window of the
   // lane is rewritten; those that still fail are listed for the warp.
   bool redo = false;
-  if (task) {
+  if constexpr (task) {
     // a task's lanes were found inexact by the launch that listed them; a
     // channel constant over the task's cells leaves exact NaN results
     redo = ((task_lanes >> lane) & 1u) && xlo < xhi && ylo < yhi;
@@ -493,10 +500,11 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
     // a channel constant over the lane's cells makes every window's variance
     // exactly zero: the item map's results (NaN) stand
     redo = need && !exact && xlo < xhi && ylo < yhi;
-    if (sc.redo_mode == 1) {
+    if constexpr (TIER == TIER_LIST) {
       // list the item's second tier as tasks of redo_rows output rows for
       // the next launch, which spreads them over every SM (the plan sizes
-      // the list for every item's tasks; a full list runs the tier here)
+      // the list for every item's tasks, so it cannot fill; if it did, the
+      // plan's status reports it)
       const uint32_t lanes = __ballot_sync(0xffffffffu, redo);
       if (lanes) {
         const int nt = (j1 - j0 + sc.redo_rows - 1) / sc.redo_rows;
@@ -509,12 +517,14 @@ __device__ __forceinline__ bool process_rows_2d_f32(const Scene2D& sc, int strip
           for (int t = lane; t < nt; t += 32)
             sc.redo_tasks[k + t] =
                 RedoTask2D{strip, j0 + t * sc.redo_rows, min(j0 + (t + 1) * sc.redo_rows, j1), lanes, slot, {0, 0, 0}};
-          redo = false;
+        } else if (lane == 0) {
+          atomicOr(status + ST_ERROR, ERRBIT_BAD_ARG);
         }
       }
+      redo = false;
     }
   }
-  if (__any_sync(0xffffffffu, redo)) {
+  if constexpr (TIER != TIER_LIST) if (__any_sync(0xffffffffu, redo)) {
     if (lane == 0) *rg.npend = 0;
     __syncwarp();
     const long long nmax = (long long)sc.kh * KW;
@@ -661,7 +671,7 @@ template <int M, int KW, bool TMA>
 __device__ __forceinline__ bool process_item_2d_f32(const Scene2D& sc, int strip, int rb, const Ring2DF& rg,
                                                     uint32_t& seq, uint32_t* status) {
   const int j0 = rb * sc.TJ;
-  return process_rows_2d_f32<M, KW, TMA>(sc, strip, j0, min(j0 + sc.TJ, sc.OH), 0u, 0, rg, seq, status);
+  return process_rows_2d_f32<M, KW, TMA, TIER_IN_PLACE>(sc, strip, j0, min(j0 + sc.TJ, sc.OH), 0u, 0, rg, seq, status);
 }
 
 }  // namespace swc

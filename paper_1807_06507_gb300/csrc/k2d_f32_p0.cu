@@ -1,8 +1,9 @@
-// k2d_f32_p0.cu -- fused 2-D float32 kernel instances for window widths 1, 3, 5, 7.
+// k2d_f32_p0.cu -- fused 2-D float32 kernel instances for window widths 1 and 3
+// (each with and without TMA, for the three second-tier placements).
 #include "k2d_f32_kern.cuh"
 
 namespace swc {
 
-SWC_K2DF_PART(k2d_f32_launch_p0, 1, 3, 5, 7)
+SWC_K2DF_PART(k2d_f32_launch_p0, 1, 3)
 
 }  // namespace swc

@@ -1,8 +1,9 @@
-// k2d_f32_p1.cu -- fused 2-D float32 kernel instances for window widths 9, 11, 13, 15.
+// k2d_f32_p1.cu -- fused 2-D float32 kernel instances for window widths 5 and 7
+// (each with and without TMA, for the three second-tier placements).
 #include "k2d_f32_kern.cuh"
 
 namespace swc {
 
-SWC_K2DF_PART(k2d_f32_launch_p1, 9, 11, 13, 15)
+SWC_K2DF_PART(k2d_f32_launch_p1, 5, 7)
 
 }  // namespace swc

@@ -1,8 +1,9 @@
-// k2d_f32_p3.cu -- fused 2-D float32 kernel instances for window widths 25, 27, 29, 31.
+// k2d_f32_p3.cu -- fused 2-D float32 kernel instances for window widths 13 and 15
+// (each with and without TMA, for the three second-tier placements).
 #include "k2d_f32_kern.cuh"
 
 namespace swc {
 
-SWC_K2DF_PART(k2d_f32_launch_p3, 25, 27, 29, 31)
+SWC_K2DF_PART(k2d_f32_launch_p3, 13, 15)
 
 }  // namespace swc

@@ -1,0 +1,9 @@
+// k2d_f32_p5.cu -- fused 2-D float32 kernel instances for window widths 21 and 23
+// (each with and without TMA, for the three second-tier placements).
+#include "k2d_f32_kern.cuh"
+
+namespace swc {
+
+SWC_K2DF_PART(k2d_f32_launch_p5, 21, 23)
+
+}  // namespace swc

@@ -53,10 +53,8 @@ struct Scene2D {
   int qbits;               // float32 path: fixed-point magnitude bits (|X| < 2^qbits)
   int wide;                // uint16 path: 64-bit second-moment sums (large windows)
   int test_stall;          // test hook: item (0, 0) never issues its first row's copy
-  // float32 second tier: 0 runs it inside the item; 1 lists it as tasks of
-  // at most redo_rows output rows (redo_tasks, redo_count, capacity
-  // redo_cap); 2 runs the listed tasks (the launch after a mode-1 launch)
-  int redo_mode;
+  // float32 second tier listed as tasks of at most redo_rows output rows
+  // (redo_tasks, redo_count, capacity redo_cap) for the launch that follows
   int redo_rows;
   int redo_cap;
   RedoTask2D* redo_tasks;

@@ -22,12 +22,18 @@ int k2d_u16_blocks_per_sm(int kw, bool wide, size_t smem);
 
 // 2-D float32: same interface.
 bool k2d_f32_geometry(int kw, Geo2DInfo* g);
-cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
-// the instances of four groups of window widths (1-7, 9-15, 17-23, 25-31)
-cudaError_t k2d_f32_launch_p0(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
-cudaError_t k2d_f32_launch_p1(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
-cudaError_t k2d_f32_launch_p2(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
-cudaError_t k2d_f32_launch_p3(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma);
+// tier: the float32 second tier's placement (0 in place, 1 listed as tasks,
+// 2 the listed tasks; k2d_f32.cuh)
+cudaError_t k2d_f32_launch(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier = 0);
+// the instances of eight pairs of window widths (1-3, 5-7, ..., 29-31)
+cudaError_t k2d_f32_launch_p0(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p1(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p2(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p3(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p4(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p5(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p6(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
+cudaError_t k2d_f32_launch_p7(int kw, const K2DParams& p, int grid, size_t smem, cudaStream_t st, bool tma, int tier);
 
 // 1-D (uint16 or float32): outputs per lane per chunk, and the launch.
 int k1d_outputs_per_lane();

@@ -849,13 +849,10 @@ static swcorr_status run_2d(swcorr_plan_s* p, const void* x, const void* y, cons
   if (p->dtype == SWCORR_F32 && p->d_redo) {
     // the items list their second tier; a second launch spreads its tasks
     // over every SM (it exits at once when nothing was listed)
-    K2DParams k2 = p->k2;
     if ((e = cudaMemsetAsync(p->d_redo, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "2-D task list reset");
-    k2.sc.redo_mode = 1;
-    if ((e = k2d_f32_launch(k2.sc.kw, k2, p->grid, p->smem, st, use_tma)) != cudaSuccess)
+    if ((e = k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma, 1)) != cudaSuccess)
       return cuda_fail(e, "2-D kernel launch");
-    k2.sc.redo_mode = 2;
-    e = k2d_f32_launch(k2.sc.kw, k2, p->grid, p->smem, st, use_tma);
+    e = k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma, 2);
   } else {
     e = p->dtype == SWCORR_F32 ? k2d_f32_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma)
                                : k2d_u16_launch(p->k2.sc.kw, p->k2, p->grid, p->smem, st, use_tma);
