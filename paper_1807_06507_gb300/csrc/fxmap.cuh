@@ -25,11 +25,13 @@
 // The kernels' float32 evaluation of Eq. 2 adds at most 7e-7 (relative
 // rounding of the int64 -> float32 conversions, the product, rsqrt and the
 // final product).  A window is certified when z_x + z_y <= 9e-6, which keeps
-// |dc| below 1e-5.  Any other window is recomputed: first from
-// its own cells with a window-local map of up to 26 bits and 64-bit sums
-// (certified the same way; X = round(x s) - M through a 64-bit conversion,
-// so rho = 1/2 and values on the grid convert exactly), and, if that fails
-// too, in FP64 in two passes (the classical formula, Introduction).
+// |dc| below 1e-5.  A block with windows that fail is computed again with a
+// finer map of the same range (fx_wide: up to 26 bits, 64-bit sums; X =
+// round(x s) - M through a 64-bit conversion, so rho = 1/2 and values on the
+// grid convert exactly), certified the same way; a window that still fails
+// is recomputed from its own cells with a window-local map of that kind
+// (fx_box_exact, fx_box_warp), and, if that fails too, in FP64 in two passes
+// (the classical formula, Introduction).
 #pragma once
 
 #include <stdint.h>
@@ -353,14 +355,6 @@ static __device__ __noinline__ float fx_box_warp(const FxBox& b, uint32_t* statu
     }
   }
   if (lane == 0 && status) atomicAdd(status + ST_FALLBACK, 1u);
-  return c;
-}
-
-// Recompute one window exactly (window-local map, else FP64) and count it.
-static __device__ __noinline__ float fx_recompute(const FxBox& b, uint32_t* status) {
-  float c;
-  if (!fx_box_exact(b, &c)) c = fx_box_fp64(b);
-  if (status) atomicAdd(status + ST_FALLBACK, 1u);
   return c;
 }
 
