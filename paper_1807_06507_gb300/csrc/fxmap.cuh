@@ -27,7 +27,7 @@
 // final product).  A window is certified when z_x + z_y <= 9e-6, which keeps
 // |dc| below 1e-5.  A block with windows that fail is computed again with a
 // finer map of the same range (fx_wide: up to 26 bits, 64-bit sums; X =
-// round(x s) - M through a 64-bit conversion, so rho = 1/2 and values on the
+// round(x s) - M with one rounding, so rho = 1/2 and values on the
 // grid convert exactly), certified the same way; a window that still fails
 // is recomputed from its own cells with a window-local map of that kind
 // (fx_box_exact, fx_box_warp), and, if that fails too, in FP64 in two passes
@@ -145,14 +145,21 @@ struct FxBox {
 
 __device__ __forceinline__ int fx_bitlen(unsigned long long v) { return 64 - __clzll(v); }
 
-// Map of a recomputation (window-local or lane-local) of n cells whose
-// values lie in [lo, hi], lo < hi: q = min(26, (62 - bitlen(n)) / 2) bits
-// (n 2^2q < 2^62 keeps the 64-bit sums of squares exact), scale s = 2^e and
-// the integer M = round(mid s).  A value converts as X = round(x s) - M in
-// 64-bit integers: x s is exact (power-of-two scale), so X is exact when x s is
-// an integer (x on the 2^-e grid) and within 1/2 otherwise.
+// Map of a recomputation (window-local, lane-, chunk- or item-wide) of n
+// cells whose values lie in [lo, hi], lo < hi: q = min(26, (62 -
+// bitlen(n)) / 2) bits (n 2^2q < 2^62 keeps the 64-bit sums of squares
+// exact), scale s = 2^e and the integer M = mid s.  A value converts as
+// X = round(x s) - M: x s is exact (power-of-two scale), so X is exact when
+// x s is an integer (x on the 2^-e grid) and within 1/2 otherwise.  It is
+// evaluated in 32 bits.  When |mid| <= 16 A (A the half range), |x s| and
+// |M| stay below 17 * 2^26: X = F2I(x s) - M.  Otherwise every x lies within
+// A < |mid| / 16 of mid, so x - mid is exact (Sterbenz), mid is on the grid
+// (its ulp, at least |mid| 2^-24 > A 2^-20, is a multiple of 2^-e) and
+// X = F2I((x - mid) s), the same integer.
 struct FxWide {
   float s;
+  float sub;  // mid for a block far from 0, else 0
+  int moff;   // M for a block near 0, else 0
   long long M;
 };
 __device__ __forceinline__ FxWide fx_wide(float lo, float hi, long long n) {
@@ -165,12 +172,15 @@ __device__ __forceinline__ FxWide fx_wide(float lo, float hi, long long n) {
   FxWide w;
   w.s = __int_as_float((127 + e) << 23);
   w.M = __float2ll_rn(mid * w.s);
+  const bool far = fabsf(mid) > 16.0f * A;
+  w.sub = far ? mid : 0.0f;
+  w.moff = far ? 0 : (int)w.M;
   return w;
 }
 __device__ __forceinline__ long long fx_wide_quant(float x, const FxWide& w, bool& on_grid) {
-  const float v = x * w.s;  // exact
+  const float v = (x - w.sub) * w.s;  // exact
   on_grid = on_grid && (fabsf(v) >= 8388608.0f || v == rintf(v));
-  return __float2ll_rn(v) - w.M;
+  return (long long)(__float2int_rn(v) - w.moff);
 }
 
 // Window-local recomputation: the box's own range and map (fx_wide), exact

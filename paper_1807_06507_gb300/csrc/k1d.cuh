@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
       int4* XW = reinterpret_cast<int4*>(X);
       int4* YW = reinterpret_cast<int4*>(Y);
       if constexpr (WIDE) {
-        // X = round(x s) - M through a 64-bit conversion (x s is exact)
+        // X = round(x s) - M, one rounding (fx_wide)
         const FxWide wx = fx_wide(xlo, xhi, p.k), wy = fx_wide(ylo, yhi, p.k);
         const bool const_ch = !(xlo < xhi) || !(ylo < yhi);  // a constant channel: every window NaN
         bool gx = true, gy = true;

@@ -405,15 +405,15 @@ __global__ void __launch_bounds__(K3_THREADS, SWC_K3D_MINB) k3d_kernel(const __g
           const int idx = r * G::BXW + G::COFF + c;
           int Xe, Xl, Ye, Yl;
           if constexpr (WIDE) {
-            // X = round(x s) - M through a 64-bit conversion (x s is exact);
-            // off-volume cells are absent (X = 0)
+            // X = round(x s) - M in 32 bits (fx_wide); off-volume cells are
+            // absent (X = 0)
             const float* pe = reinterpret_cast<const float*>(se);
             const float* pl = reinterpret_cast<const float*>(sl);
             const bool ie = ue && row_ok, il = ul && row_ok;
-            Xe = ie ? (int)(__float2ll_rn(pe[idx] * sh_wx.s) - sh_wx.M) : 0;
-            Ye = ie ? (int)(__float2ll_rn(pe[yoff + idx] * sh_wy.s) - sh_wy.M) : 0;
-            Xl = il ? (int)(__float2ll_rn(pl[idx] * sh_wx.s) - sh_wx.M) : 0;
-            Yl = il ? (int)(__float2ll_rn(pl[yoff + idx] * sh_wy.s) - sh_wy.M) : 0;
+            Xe = ie ? __float2int_rn((pe[idx] - sh_wx.sub) * sh_wx.s) - sh_wx.moff : 0;
+            Ye = ie ? __float2int_rn((pe[yoff + idx] - sh_wy.sub) * sh_wy.s) - sh_wy.moff : 0;
+            Xl = il ? __float2int_rn((pl[idx] - sh_wx.sub) * sh_wx.s) - sh_wx.moff : 0;
+            Yl = il ? __float2int_rn((pl[yoff + idx] - sh_wy.sub) * sh_wy.s) - sh_wy.moff : 0;
           } else if (p.is_f32) {
             const float* pe = reinterpret_cast<const float*>(se);
             const float* pl = reinterpret_cast<const float*>(sl);
