@@ -87,7 +87,9 @@ typedef enum { SWCORR_U16 = 1, SWCORR_F32 = 2 } swcorr_dtype;
  *                         past an edge of the grid gives -2, and so does a
  *                         window holding a missing value (a value <= -999) in
  *                         x or in y; other windows as with CLIP (they are whole).
- *                         Served by the general n-D path. */
+ *                         1-D to 3-D: the fused kernel, then a pass that
+ *                         writes the -2 outputs (the output must then be
+ *                         contiguous); other plans: the general n-D path. */
 typedef enum { SWCORR_BORDER_CLIP = 0, SWCORR_BORDER_PAPER = 1 } swcorr_border;
 
 enum {
@@ -125,9 +127,10 @@ typedef struct swcorr_plan_s* swcorr_plan;
  * equal-size grids, Section 3: both data sets have the same size; window
  * size and step, Introduction).
  *   out    : receives the plan (set to NULL on failure).
- *   ndim   : 1 to 8.  1-D, 2-D and 3-D grids with clipped windows run one
- *            fused kernel (Section 1, steps 1-4 in one pass over HBM); more
- *            dimensions, the paper's border rule and SWCORR_FLAG_SAT run the
+ *   ndim   : 1 to 8.  1-D, 2-D and 3-D grids run one fused kernel
+ *            (Section 1, steps 1-4 in one pass over HBM; under the paper's
+ *            border rule followed by a pass that writes the -2 outputs); more
+ *            dimensions, SWCORR_FLAG_SAT and SWCORR_FLAG_UNFUSED run the
  *            general path (the steps as separate passes over materialised
  *            sums, one per dimension: Section 1's n-dimensional
  *            generalisation, Section 2's parallel phases).

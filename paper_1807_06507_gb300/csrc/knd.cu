@@ -28,7 +28,15 @@
 //    an edge or with a missing cell under the paper's convention; Eq. 2 in
 //    128-bit integers, one float32 rounding per factor; NaN for a zero
 //    variance; clamp to [-1, 1].
+//  * Mask-only form: after a fused kernel has written every window with
+//    clipped borders, the paper's convention needs only the -2 outputs: one
+//    stream (the missing-cell count, float32 only), its sliding sums, and a
+//    finalize that writes -2 and nothing else (a window that neither passes
+//    an edge nor holds a missing cell is whole, so the fused result is the
+//    convention's result).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "fxmap.cuh"
@@ -112,6 +120,10 @@ __global__ void __launch_bounds__(kThreads) nd_convert(KNDParams p) {
     float a, b;
     load_cell(p, in_offset(p, c), a, b);
     const bool miss = p.paper && (a <= -999.0f || b <= -999.0f);
+    if (p.mask_only) {
+      S[c] = miss ? 1 : 0;
+      continue;
+    }
     long long X = 0, Y = 0;
     if (!miss) {
       if (p.is_f32) {
@@ -398,6 +410,10 @@ __global__ void __launch_bounds__(kThreads) nd_finalize(KNDParams p, const long 
       p.out[o] = -2.0f;
       continue;
     }
+    if (p.mask_only) {  // (uint16 grids hold no missing value)
+      if (p.is_f32 && W[centre_cell] > 0) p.out[o] = -2.0f;
+      continue;
+    }
     long long S[6];
     if (!p.sat) {
       for (int s = 0; s < p.nstreams; s++) S[s] = W[s * p.ncell + centre_cell];
@@ -445,12 +461,76 @@ __global__ void __launch_bounds__(kThreads) nd_finalize(KNDParams p, const long 
   if (recomputed) atomicAdd(p.status + ST_FALLBACK, recomputed);
 }
 
+// Mask-only form: -2 over the outputs whose index along d lies in [j0, j1)
+// (one slab of windows that pass an edge of dimension d); inner = outputs
+// per step of index d.
+__global__ void __launch_bounds__(kThreads) nd_border_slab(KNDParams p, int d, long long j0, long long j1,
+                                                           long long inner) {
+  const long long width = j1 - j0, total = width * (p.nout / p.oshape[d]);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long in = t % inner, rest = t / inner;
+    const long long j = j0 + rest % width, outer = rest / width;
+    p.out[(outer * p.oshape[d] + j) * inner + in] = -2.0f;
+  }
+}
+
+// Mask-only form, float32: -2 over the outputs whose window holds a missing
+// cell (the summed count W at the window's centre), 32-bit index arithmetic
+// (the plan keeps this form to outputs and cells below 2^31).
+__global__ void __launch_bounds__(kThreads) nd_mask_apply(KNDParams p, const long long* W) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < (int)p.nout; o += gridDim.x * blockDim.x) {
+    int rem = o;
+    long long centre = 0;
+    for (int d = p.ndim - 1; d >= 0; d--) {
+      const int od = (int)p.oshape[d];
+      const int j = rem % od;
+      rem /= od;
+      centre += (long long)j * p.stride[d] * p.inner[d];
+    }
+    if (W[centre] > 0) p.out[o] = -2.0f;
+  }
+}
+
 }  // namespace
+
+// The mask-only form's -2 over the windows that pass an edge: two slabs per
+// dimension.
+static cudaError_t knd_border(const KNDParams& p, int blocks, cudaStream_t st) {
+  long long inner = 1;
+  for (int d = p.ndim - 1; d >= 0; d--) {
+    const long long O = p.oshape[d], s = p.stride[d], N = p.shape[d];
+    // low side: j s - h1 < 0; high side: j s + h2 > N - 1
+    const long long a = std::min(O, (p.h1[d] + s - 1) / s);
+    const long long b = N - 1 - p.h2[d] < 0 ? 0 : std::min(O, (N - 1 - p.h2[d]) / s + 1);
+    if (a > 0) nd_border_slab<<<blocks, kThreads, 0, st>>>(p, d, 0, a, inner);
+    if (std::max(a, b) < O) nd_border_slab<<<blocks, kThreads, 0, st>>>(p, d, std::max(a, b), O, inner);
+    inner *= O;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t knd_launch(const KNDParams& p, int sms, cudaStream_t st) {
   const int blocks = sms * 8;
+  if (p.mask_only) {
+    cudaError_t e = cudaSuccess;
+    if (p.is_f32) {  // the missing-cell count, summed over each window, then applied
+      nd_init<<<1, 1, 0, st>>>(p);
+      nd_convert<<<blocks, kThreads, 0, st>>>(p);
+      int cur = 0;
+      for (int d = 0; d < p.ndim; d++) {
+        if (d < p.ndim - 1)
+          nd_pass_lines<<<blocks, kThreads, 0, st>>>(p, d, p.buf[cur], p.buf[cur ^ 1]);
+        else
+          nd_pass_inner<<<blocks, kThreads, 0, st>>>(p, p.buf[cur], p.buf[cur ^ 1]);
+        cur ^= 1;
+      }
+      nd_mask_apply<<<blocks, kThreads, 0, st>>>(p, p.buf[cur]);
+      e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? knd_border(p, blocks, st) : e;
+  }
   nd_init<<<1, 1, 0, st>>>(p);
-  if (p.is_f32) nd_range<<<blocks, kThreads, 0, st>>>(p);
+  if (p.is_f32 && !p.mask_only) nd_range<<<blocks, kThreads, 0, st>>>(p);
   nd_convert<<<blocks, kThreads, 0, st>>>(p);
   int cur = 0;
   for (int d = 0; d < p.ndim; d++) {

@@ -17,8 +17,12 @@ struct KNDParams {
   int stride[KND_MAXDIM];
   long long oshape[KND_MAXDIM];  // ceil(shape / stride)
   long long ncell, nout;
-  int nstreams;                  // 5, or 6 with the missing-cell count
+  int nstreams;                  // 5, or 6 with the missing-cell count (1 when mask_only)
   int is_f32, paper, sat, qbits;
+  int mask_only;                 // the paper's convention after a fused kernel: only the
+                                 //   missing-cell count is summed; the finalize writes -2 where
+                                 //   the window passes an edge or holds a missing cell and leaves
+                                 //   every other output as the fused kernel wrote it
   const void* x;
   const void* y;
   float* out;                    // contiguous output

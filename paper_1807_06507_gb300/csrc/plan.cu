@@ -305,6 +305,11 @@ struct swcorr_plan_s {
   // scratch)
   KNDParams kn{};
   void* d_nd = nullptr;
+  // the paper's -2 convention on a fused kernel: the fused run, then the
+  // general path's mask-only pass (its missing-count buffers in d_mask)
+  bool paper_post = false;
+  KNDParams kmask{};
+  void* d_mask = nullptr;
   // tensor-map cache
   const void* cached_x = nullptr;
   const void* cached_y = nullptr;
@@ -692,8 +697,7 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     return fail(SWCORR_ERR_INVALID_ARG, "unknown border rule %d", (int)border);
   if (flags & ~(uint32_t)(SWCORR_FLAG_EMIT_SUMS | SWCORR_FLAG_TEST_STALL | SWCORR_FLAG_SAT | SWCORR_FLAG_UNFUSED))
     return fail(SWCORR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
-  const bool general =
-      ndim > 3 || border == SWCORR_BORDER_PAPER || (flags & (SWCORR_FLAG_SAT | SWCORR_FLAG_UNFUSED));
+  const bool general = ndim > 3 || (flags & (SWCORR_FLAG_SAT | SWCORR_FLAG_UNFUSED));
   if ((flags & SWCORR_FLAG_TEST_STALL) && general)
     return fail(SWCORR_ERR_INVALID_ARG, "SWCORR_FLAG_TEST_STALL applies to 2-D uint16 plans");
   if ((flags & SWCORR_FLAG_TEST_STALL) && !(ndim == 2 && dtype == SWCORR_U16))
@@ -748,6 +752,23 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
       g_last_error.clear();
       tmp.kind = KIND_ND;
       st = plan_nd(&tmp);
+    } else if (st == SWCORR_OK && border == SWCORR_BORDER_PAPER) {
+      // the fused kernel writes every window with clipped borders; a window
+      // that neither passes an edge nor holds a missing value is whole, so
+      // only the -2 outputs remain: the general path's mask-only pass
+      swcorr_plan_s t2 = tmp;
+      t2.kind = KIND_ND;
+      st = plan_nd(&t2);
+      if (st == SWCORR_OK && (t2.kn.nout >= (1ll << 31) || t2.kn.ncell >= (1ll << 31))) {
+        // (the mask pass indexes in 32 bits): the general path instead
+        tmp = t2;
+      } else if (st == SWCORR_OK) {
+        tmp.paper_post = true;
+        tmp.kmask = t2.kn;
+        tmp.kmask.mask_only = 1;
+        tmp.kmask.nstreams = 1;
+        tmp.kmask.sat = 0;
+      }
     }
   }
   if (st != SWCORR_OK) return st;
@@ -766,6 +787,17 @@ swcorr_status swcorr_plan_create_tuned(swcorr_plan* out, int ndim, const int64_t
     return cuda_fail(e, "cudaMemset(status)");
   }
   p->k2.status = p->d_status;
+  if (p->paper_post) {
+    // float32: two missing-count buffers (int64 per cell) and the scratch
+    // words; uint16 holds no missing value and needs the scratch only
+    const size_t bytes = p->dtype == SWCORR_F32 ? 2 * (size_t)p->kmask.ncell * 8 + 64 : 64;
+    e = cudaMalloc(&p->d_mask, bytes);
+    if (e != cudaSuccess) {
+      swcorr_plan_destroy(p);
+      return e == cudaErrorMemoryAllocation ? fail(SWCORR_ERR_OOM, "-2 mask buffers (%zu B): out of device memory", bytes)
+                                            : cuda_fail(e, "cudaMalloc(-2 mask buffers)");
+    }
+  }
   if (p->kind == KIND_2D_F32) {
     // second-tier tasks of at most redo_rows output rows: every item can list
     // all of its rows once, so the list never fills
@@ -861,6 +893,34 @@ static swcorr_status run_2d(swcorr_plan_s* p, const void* x, const void* y, cons
   return SWCORR_OK;
 }
 
+// The -2 outputs of the paper's convention after a fused run (knd.cu's
+// mask-only form).
+static swcorr_status run_mask(swcorr_plan_s* p, const void* x, const void* y, const int64_t* in_pitch, float* c,
+                              cudaStream_t st) {
+  KNDParams& km = p->kmask;
+  if (in_pitch) {
+    if (in_pitch[p->ndim - 1] != 1) return fail(SWCORR_ERR_UNSUPPORTED, "in_pitch[ndim-1] must be 1");
+    for (int d = 0; d < p->ndim - 1; d++)
+      if (in_pitch[d] < in_pitch[d + 1] * p->shape[d + 1])
+        return fail(SWCORR_ERR_INVALID_ARG, "in_pitch[%d] too small", d);
+  }
+  for (int d = 0; d < p->ndim; d++) km.ipitch[d] = in_pitch ? in_pitch[d] : km.inner[d];
+  km.x = x;
+  km.y = y;
+  km.out = c;
+  km.sums = nullptr;
+  unsigned char* base = static_cast<unsigned char*>(p->d_mask);
+  const size_t bytes = p->dtype == SWCORR_F32 ? (size_t)km.ncell * 8 : 0;
+  km.buf[0] = reinterpret_cast<long long*>(base);
+  km.buf[1] = reinterpret_cast<long long*>(base + bytes);
+  km.scratch = reinterpret_cast<float*>(base + 2 * bytes);
+  km.segs = nullptr;
+  km.status = p->d_status;
+  cudaError_t e = knd_launch(km, p->dev.sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "-2 mask launch");
+  return SWCORR_OK;
+}
+
 swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int64_t* in_pitch, float* c,
                          const int64_t* out_pitch, int64_t* sums, void* stream) {
   g_last_error.clear();
@@ -873,6 +933,30 @@ swcorr_status swcorr_run(swcorr_plan p, const void* x, const void* y, const int6
     return fail(SWCORR_ERR_INVALID_ARG, "plan has SWCORR_FLAG_EMIT_SUMS: sums must not be NULL");
   if (!(p->flags & SWCORR_FLAG_EMIT_SUMS)) sums = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (p->paper_post) {
+    if (out_pitch) {
+      int64_t want = 1;
+      for (int d = p->ndim - 1; d >= 0; d--) {
+        if (out_pitch[d] != want) return fail(SWCORR_ERR_UNSUPPORTED, "the -2 convention writes a contiguous output");
+        want *= p->oshape[d];
+      }
+    }
+    swcorr_status s0 = SWCORR_OK;
+    switch (p->kind) {
+      case KIND_2D_U16:
+      case KIND_2D_F32: s0 = run_2d(p, x, y, in_pitch, c, out_pitch, nullptr, st); break;
+      case KIND_3D: p->k3.sums = nullptr; s0 = run_3d(p, x, y, in_pitch, c, out_pitch, st); break;
+      case KIND_1D:
+        if ((in_pitch && in_pitch[0] != 1) || (out_pitch && out_pitch[0] != 1))
+          return fail(SWCORR_ERR_UNSUPPORTED, "1-D series must be contiguous");
+        p->k1.sums = nullptr;
+        s0 = run_1d(p, x, y, c, st);
+        break;
+      default: return fail(SWCORR_ERR_UNSUPPORTED, "plan kind %d cannot run", p->kind);
+    }
+    if (s0 != SWCORR_OK) return s0;
+    return run_mask(p, x, y, in_pitch, c, st);
+  }
   switch (p->kind) {
     case KIND_ND: return run_nd(p, x, y, in_pitch, c, out_pitch, sums, st);
     case KIND_2D_U16:
@@ -1107,7 +1191,7 @@ swcorr_status swcorr_run_host(swcorr_plan p, const void* x, const void* y, float
   if (p->kind != KIND_ND && p->ndim >= 2 && (inner * (int64_t)elem_size(p->dtype)) % 16 != 0)
     return fail(SWCORR_ERR_ALIGNMENT, "host runs need rows of a multiple of 16 bytes (got %lld elements)",
                 (long long)inner);
-  if (p->kind == KIND_2D_U16 || p->kind == KIND_2D_F32) return run_host_2d_banded(p, x, y, c, st);
+  if ((p->kind == KIND_2D_U16 || p->kind == KIND_2D_F32) && !p->paper_post) return run_host_2d_banded(p, x, y, c, st);
   if ((e = cudaMemcpyAsync(p->d_x, x, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "copy x to device");
   if ((e = cudaMemcpyAsync(p->d_y, y, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -1149,6 +1233,7 @@ void swcorr_plan_destroy(swcorr_plan p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->d_batch);
   cudaFree(p->d_nd);
+  cudaFree(p->d_mask);
   cudaFree(p->d_redo);
   cudaFree(p->d_status);
   cudaFree(p->d_x);
