@@ -515,8 +515,11 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     const int e_in = e_out + p.k;         // first cell to enter after it
     float res[M1];
     uint64_t fail = 0;  // outputs whose certificate's quick test failed
+    // the wide form runs on a few chunks per launch: a rolled slide keeps its
+    // 128-bit finalize from filling a cold instruction cache
+    constexpr int kSlideUnroll = WIDE ? 1 : M1;
     if constexpr (UNIT) {  // stride 1
-#pragma unroll
+#pragma unroll kSlideUnroll
       for (int t = 0; t < M1; t++) {
         bool f;
         if constexpr (WIDE)
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
         }
       }
     } else {
-#pragma unroll
+#pragma unroll kSlideUnroll
       for (int t = 0; t < M1; t++) {
         bool f;
         if constexpr (WIDE)
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(128, 3) k1d_kernel(const __grid_constant__ K1D
     // once every warp of the CTA is done reading it
     __syncthreads();
     float* sw = reinterpret_cast<float*>(X) + warp * LW;
-#pragma unroll
+#pragma unroll kSlideUnroll
     for (int t = 0; t < M1; t++) sw[lane * M1 + t] = res[t];
     __syncwarp();
     const long long wc0 = c0 + (long long)warp * LW;
